@@ -1,0 +1,100 @@
+"""Pins of the oracle's ray tracer and path-time integrator (Sec. 5)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2302_10988_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    out = {}
+    for l in open(os.path.join(GOLDEN, "velocity_gradient_ray.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            out[k] = float(v)
+    return out
+
+
+def _gradient_medium(oracle):
+    wl = W.velocity_gradient()
+    s = wl.samples[0]
+    mats = [oracle.mat_from_voigt(c6, rho) for c6, rho in wl.materials]
+    return oracle.OMedium.from_regions(s.nx, s.ny, s.h, s.region_map, s.region_theta, wl.region_material, mats)
+
+
+def _circle():
+    """Circle through source and receiver for v = v0 + g x (Sec. 5.2, Eq. circle_vel_grad), with the
+    relation between the launch angle and the receiver written without the print's dropped factor 2:
+    g^2 y'^2 + (g x' + v0)^2 - v0^2 = 2 g y' v0 cot(theta0)."""
+    g, v0 = 21.0, 3021.0
+    xp, yp = 198.0, 150.0
+    cot = ((g * yp) ** 2 + (g * xp + v0) ** 2 - v0 ** 2) / (2 * g * yp * v0)
+    return 1.0 - v0 / g, 30.0 + v0 * cot / g, v0 * np.sqrt(1.0 + cot * cot) / g
+
+
+def test_circle_matches_printed_geometry():
+    G = _golden()
+    cx, cy, R = _circle()
+    assert cx == pytest.approx(G["circle_centre_x"], abs=1e-3)
+    assert cy == pytest.approx(G["circle_centre_y"], abs=1e-3)
+    assert R == pytest.approx(G["circle_radius"], abs=1e-3)
+
+
+def test_path_time_of_true_arc(oracle):
+    """Integrating the exact arc through the nearest-node cells gives the paper's time of the true
+    path on the discretised grid; the continuum time (1/g) arccosh(1 + g^2 d^2 / (2 v_a v_b)) is
+    close to it."""
+    G = _golden()
+    M = _gradient_medium(oracle)
+    cx, cy, R = _circle()
+    a0, a1 = np.arctan2(30 - cy, 1 - cx), np.arctan2(180 - cy, 199 - cx)
+    aa = np.linspace(a0, a1, 20001)
+    arc = np.stack([cx + R * np.cos(aa), cy + R * np.sin(aa)], 1)
+    t = oracle.path_time(M, arc)
+    assert t == pytest.approx(G["true_time_discretised"], rel=2e-6)
+    g = 21.0
+    cont = np.arccosh(1 + g * g * (198.0 ** 2 + 150.0 ** 2) / (2 * 3021.0 * 7179.0)) / g * 1e-3
+    assert t == pytest.approx(cont, rel=1e-5)
+
+
+def test_velocity_gradient_ray(oracle):
+    """Sec. 5.2: the traced ray follows the circular arc (paper: within about 0.3 cells) and its
+    integrated time is within a few 1e-5 of the true path's (paper: 7e-6)."""
+    G = _golden()
+    M = _gradient_medium(oracle)
+    fr, t0 = oracle.init_hierarchy(M, 1, 30)
+    tau, rec, st = oracle.fmm(M, fr, t0)
+    pts, status = oracle.trace_ray(M, tau, (199, 180), (1, 30))
+    assert status == 0
+    assert tuple(pts[0]) == (199.0, 180.0) and tuple(pts[-1]) == (1.0, 30.0)
+    cx, cy, R = _circle()
+    dev = np.abs(np.hypot(pts[:, 0] - cx, pts[:, 1] - cy) - R)
+    assert dev.max() < 0.5
+    t = oracle.path_time(M, pts)
+    assert t >= G["true_time_discretised"] * (1 - 1e-6)
+    assert t == pytest.approx(G["ray_time"], rel=1e-4)
+
+
+def test_homogeneous_ray_is_straight(oracle):
+    """Sec. 5.3: in a homogeneous medium the fastest path is the straight segment."""
+    n = 80
+    c6, rho = W.WELD_TI
+    m = oracle.mat_from_voigt(c6, rho)
+    for th in (0.0, 0.6, -1.1):
+        M = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m])
+        fr, t0 = oracle.init_hierarchy(M, 10, 0)
+        tau = oracle.fmm(M, fr, t0)[0]
+        for rec in ((70, 79), (10, 79), (79, 40)):
+            pts, st = oracle.trace_ray(M, tau, rec, (10, 0))
+            assert st == 0
+            a = np.array([10.0, 0.0])
+            b = np.array(rec, float)
+            u = (b - a) / np.linalg.norm(b - a)
+            off = np.abs((pts - a) @ np.array([-u[1], u[0]]))
+            assert off.max() < 1.5  # the field's angle-dependent error bends the ray by about a cell
+            straight = np.linalg.norm(b - a) * 1e-3 / oracle.group_exact(m, np.arctan2(*(b - a)[::-1]) - th)[1]
+            t = oracle.path_time(M, pts)
+            assert straight * (1 - 0.006) <= t <= straight * 1.01
