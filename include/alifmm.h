@@ -1,0 +1,235 @@
+/*
+ * alifmm.h -- C ABI of the GB300 (sm_103a) ALI-FMM travel-time library.
+ *
+ * The library computes first-arrival qP travel-time fields in 2D heterogeneous
+ * orthotropic media with the Anisotropic Locally Interpolated Fast Marching
+ * Method of Ludlam, Tant, Dolean and Curtis ("Travel times and ray paths for
+ * acoustic and elastic waves in generally anisotropic media", arXiv 2302.10988),
+ * for many sources and many media samples at once; it then traces rays back
+ * through those fields and returns the adjoint gradient of a receiver-time
+ * misfit with respect to region orientations.
+ *
+ * Problem statement (Sec. 2 and Sec. 6 of the paper): a stiffness tensor and a
+ * density per material, a grain-orientation map on a grid, and source and
+ * receiver nodes go in; travel-time fields, receiver times and ray paths come
+ * out.
+ *
+ * Conventions (all entry points)
+ *  - Grid node (i, j) is at x = i*h, y = j*h.  Fields are stored row-major,
+ *    node (i, j) of a field at offset j*nx + i.
+ *  - A "field" is one (sample b, source s) pair, numbered f = b*S + s.  The
+ *    fields of a plan are packed back to back; alf_plan_field_offset() gives
+ *    the first node of each.
+ *  - Angles are radians.  An orientation is the CCW angle from +x to the
+ *    material's phase-angle-zero axis (the axis along which the qP phase
+ *    speed is sqrt(c22/rho)), Sec. 3.2.
+ *  - SI units: Pa, kg/m^3, m, s.
+ *  - Unless a parameter says "host", pointers are CUDA device pointers owned
+ *    by the caller; the library never frees them.  The library owns only the
+ *    workspaces inside alf_ctx and alf_plan.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call that takes a stream only enqueues work on it and
+ *    returns without synchronising, unless stated otherwise.
+ *  - Every call returns an alf_status.  Arguments are validated on the host
+ *    before anything is launched; on failure nothing is enqueued and
+ *    alf_last_error() describes the problem.  Kernels never trap: device-side
+ *    failures (no convergence, a queue wait that ran out, an incomplete ray)
+ *    are written to the plan's status words and read back by
+ *    alf_sync_status().
+ */
+#ifndef ALIFMM_H
+#define ALIFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ALF_OK = 0,
+    ALF_ERR_INVALID_ARG = 1,          /* a pointer, size or option is out of range */
+    ALF_ERR_NONPHYSICAL_MATERIAL = 2, /* rho <= 0, non-finite stiffness, or qP lambda <= 0 */
+    ALF_ERR_OUT_OF_GRID = 3,          /* a source or receiver node lies outside its grid */
+    ALF_ERR_CUDA = 4,                 /* a CUDA runtime call failed (message has the CUDA error) */
+    ALF_ERR_OOM = 5,                  /* a workspace allocation failed */
+    ALF_ERR_NOT_CONVERGED = 6,        /* the sweeps hit their visit cap before reaching the fixed point */
+    ALF_ERR_RAY_INCOMPLETE = 7,       /* a ray hit its point cap before reaching its target */
+    ALF_ERR_UNSUPPORTED = 8,          /* a feature not available in this build */
+    ALF_ERR_QUEUE_TIMEOUT = 9         /* a device-side work-queue wait ran out (bounded spin) */
+} alf_status;
+
+typedef enum { ALF_FP64 = 0, ALF_FP32 = 1 } alf_precision;
+
+/* Straight-ray (group) speed model, used by the near-source initialisation,
+ * by the no-stencil fallback and by ray segments:
+ *  ALF_GROUP_PAPER: the paper's group->phase inversion (Sec. 3.2, Eqs.
+ *                   eigen_eq2, eigen_eq3, lambda_1): the phase angle whose qP
+ *                   polarisation lies along the group angle, |V| = |v|/cos(theta-phi);
+ *  ALF_GROUP_EXACT: the ray velocity of the qP slowness curve, psi = theta +
+ *                   atan(v'/v), |V| = sqrt(v^2 + v'^2), by an FP64 Newton solve. */
+typedef enum { ALF_GROUP_PAPER = 0, ALF_GROUP_EXACT = 1 } alf_group_model;
+
+/* Near-source initialisation (Sec. 4.4):
+ *  ALF_INIT_RADIUS:    nodes within Chebyshev distance init_radius of the
+ *                      source get straight-ray times (exact while the medium
+ *                      around the source is homogeneous);
+ *  ALF_INIT_HIERARCHY: the paper's refined grids (densities level_density[],
+ *                      out to level_radius[] original cells), straight rays
+ *                      inside the source cell on the finest one. */
+typedef enum { ALF_INIT_RADIUS = 0, ALF_INIT_HIERARCHY = 1 } alf_init_mode;
+
+/* One material: 6x6 Voigt stiffness (Pa) and density (kg/m^3).  Only the
+ * YZ-plane entries c22 = c[1][1], c23 = c[1][2], c33 = c[2][2], c44 = c[3][3]
+ * enter the in-plane qP speed (Sec. 3.2); a material with c22 == c33 and
+ * c23 == c22 - 2*c44 is treated as isotropic with speed sqrt(c22/rho). */
+typedef struct {
+    double c[6][6];
+    double rho;
+} alf_material;
+
+typedef struct {
+    int precision;          /* alf_precision of the sweeps and of every float output */
+    int group_model;        /* alf_group_model */
+    int init_mode;          /* alf_init_mode */
+    int init_radius;        /* ALF_INIT_RADIUS: 0..8 (default 2) */
+    int n_levels;           /* ALF_INIT_HIERARCHY: 1..4 levels (default 3) */
+    int level_density[4];   /* odd, decreasing, > 1 (default 27, 9, 3) */
+    int level_radius[4];    /* original cells, increasing (default 1, 6, 13) */
+    int plane_step;         /* ray tracer plane spacing, cells (default 4) */
+    int ray_halfwidth;      /* candidate nodes each side of the predicted crossing (default 8, max 16) */
+    double stop_radius;     /* stop when this close to the target, cells (default 1.6) */
+    int max_ray_points;     /* points per ray including both ends (default 512) */
+    int max_rounds;         /* livelock guard: sweep rounds per field <= max_rounds * (nx + ny) (default 64) */
+    int cta_threads;        /* threads per sweep CTA (one field per warp): 128, 256 or 512; 0 = autotune */
+    int ctas_per_sm;        /* persistent sweep CTAs per SM, 0 = as many as fit (default 0) */
+    int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
+    double band_cells;      /* sweep schedule: nodes later than the front by more than this many
+                               cell-crossing times wait for the front (default 4; <= 0: no band) */
+} alf_options;
+
+/* Fills `opt` with the defaults listed above.  Never fails. */
+void alf_default_options(alf_options* opt);
+
+/* Geometry of a batch: nsamples media on their own grids, all sharing the
+ * region->material table, each with the same number of sources and receivers.
+ * Every pointer here is HOST memory, read during alf_plan_create() only.
+ *  nx[b], ny[b]   grid size of sample b, 2..16384 each, nx*ny <= 2^28
+ *  h[b]           node spacing of sample b (m), > 0
+ *  region_map     uint16 region id per node, samples packed back to back,
+ *                 sample b is [ny[b]][nx[b]]
+ *  region_material[r]  material index of region r (< nmaterials)
+ *  src_ij[b][s][2], rec_ij[b][r][2]  (i, j) nodes, inside the sample's grid */
+typedef struct {
+    int nsamples;
+    const int32_t* nx;
+    const int32_t* ny;
+    const double* h;
+    const uint16_t* region_map;
+    int nregions;
+    const uint16_t* region_material;
+    int nmaterials;
+    const alf_material* materials;
+    int nsources;
+    const int32_t* src_ij;
+    int nreceivers;
+    const int32_t* rec_ij;
+} alf_geometry;
+
+typedef struct alf_ctx alf_ctx;
+typedef struct alf_plan alf_plan;
+
+/* Context on one CUDA device (made current for every call of the context).
+ * Errors: ALF_ERR_INVALID_ARG (out == NULL), ALF_ERR_CUDA (no such device, or
+ * not an sm_103 device). */
+alf_status alf_create(alf_ctx** out, int cuda_device);
+alf_status alf_destroy(alf_ctx* ctx);
+/* Message of the last failed call on `ctx` (thread-unsafe; "" if none). */
+const char* alf_last_error(const alf_ctx* ctx);
+
+/* Builds a plan: validates materials (Sec. 3.2 constants), grids, sources and
+ * receivers; uploads the geometry and allocates the sweep workspaces (per-CTA
+ * active lists and bitmaps, per-region tables).  Options are copied; NULL
+ * means defaults.  Synchronous. */
+alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* geom, const alf_options* opt, alf_plan** out);
+alf_status alf_plan_destroy(alf_plan* plan);
+/* Node offset of field f in the packed times buffer; total_nodes for f = nfields. */
+size_t alf_plan_field_offset(const alf_plan* plan, int field);
+int alf_plan_nfields(const alf_plan* plan);
+/* Options in effect (after autotuning, if it ran). */
+alf_status alf_plan_options(const alf_plan* plan, alf_options* out);
+
+/* Forward solve (Secs. 2, 4): for every field, the near-source initialisation
+ * then the ALI local update iterated to its fixed point (the heap FMM's
+ * result) by a persistent sweep kernel: each warp takes whole fields and
+ * re-evaluates the dirty set of nodes whose neighbourhood changed until it is
+ * empty.
+ *  region_theta   [nsamples][nregions] double, orientation of each region
+ *  times          [total nodes] float (ALF_FP32) or double (ALF_FP64), output
+ *  rec_times      [nsamples][nsources][nreceivers], same dtype, output; may be NULL
+ *  records        [total nodes] uint8 stencil record per node, output; may be NULL:
+ *                 0..31 stencil row 2*(pair-1)+(member-1) (Sec. 4.1 tables),
+ *                 32+k fallback through diamond slot k, 254 frozen, 255 none.
+ *                 Diamond slot order: (-1,0) (1,0) (0,-1) (0,1) (-1,-1) (1,-1)
+ *                 (-1,1) (1,1) (-2,0) (2,0) (0,-2) (0,2).
+ * Status is recorded per plan; read it with alf_sync_status(). */
+alf_status alf_solve(alf_plan* plan, const double* region_theta, void* times, void* rec_times, uint8_t* records,
+                     void* stream);
+
+/* FP64 convergence check (the precision policy's final check): evaluates the
+ * local update F in double precision at every node of a solved field and
+ * writes per field the largest |F64(tau) - tau| / tau and the number of nodes
+ * whose FP64 stencil record differs from `records` (if given).
+ *  times        solved fields (precision of the plan), input
+ *  records      records of that solve, or NULL
+ *  max_rel      [nfields] double, output
+ *  n_flips      [nfields] int32, output (0 when records is NULL) */
+alf_status alf_check64(alf_plan* plan, const double* region_theta, const void* times, const uint8_t* records,
+                       double* max_rel, int32_t* n_flips, void* stream);
+
+/* Ray tracing (Sec. 5.1) for every (sample, source, receiver): the ray starts
+ * at the receiver and walks plane by plane to the source through the source's
+ * field (reciprocity), choosing the plane family most perpendicular to the last
+ * segment and the lowest parabola vertex of cost(C) = |BC|/V_group + tau(C).
+ *  times      solved fields, input
+ *  ray_pts    [nsamples][nsources][nreceivers][max_ray_points][2] (x, y) in
+ *             grid units, same dtype as times, output
+ *  ray_npts   [.. same ..] int32 point count, output
+ *  ray_time   [.. same ..] time integrated along the path through the
+ *             nearest-node cells, same dtype, output; may be NULL
+ *  ray_status [.. same ..] int32: 0 ok, 1 point cap reached, output; may be NULL */
+alf_status alf_trace_rays(alf_plan* plan, const double* region_theta, const void* times, void* ray_pts,
+                          int32_t* ray_npts, void* ray_time, int32_t* ray_status, void* stream);
+
+/* Adjoint (reverse-mode) gradient of the receiver times: given dL/dT at every
+ * receiver, returns dL/dtheta for every region, by differentiating the chosen
+ * stencil (or fallback) of every node and the straight-ray initialisation,
+ * swept in reverse causal order.  Needs a plan created with keep_records = 1
+ * and the times and records of the same solve.
+ *  dL_drec      [nsamples][nsources][nreceivers], dtype of the plan, input
+ *  dL_dtheta    [nsamples][nregions] double, output (overwritten) */
+alf_status alf_backward(alf_plan* plan, const double* region_theta, const void* times, const uint8_t* records,
+                        const void* dL_drec, double* dL_dtheta, void* stream);
+
+/* Synchronises `stream` and returns in *worst (host) the first non-OK device
+ * status recorded by the plan since the last call (then clears it), and the
+ * matching alf_status as the return value. */
+alf_status alf_sync_status(alf_plan* plan, void* stream, int32_t* worst);
+
+/* Work counters of the last alf_solve on `stream` (synchronises `stream`):
+ *  out[0] node evaluations of the sweep kernel, out[1] sweep rounds over all
+ *  fields, out[2] nodes in the plan, out[3] persistent CTAs launched. */
+alf_status alf_plan_stats(alf_plan* plan, void* stream, uint64_t out[4]);
+
+/* Velocity model on the device, for checks: out[k] = qP phase speed (kind 0)
+ * or group speed (kind 1, model `group_model`) of material *mat (host) at
+ * angle angles[k] relative to the material axis, computed in `precision`.
+ *  angles, out  device double arrays of n entries */
+alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, int group_model, int precision,
+                             const double* angles, double* out, int n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALIFMM_H */

@@ -1,0 +1,569 @@
+// alf_api.cu -- the C ABI declared in include/alifmm.h: validation, plan
+// layout (fields, tiles, work queue), workspace ownership and launch order.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "alf_internal.h"
+
+using namespace alf;
+
+namespace {
+
+alf_status fail(alf_ctx* ctx, alf_status code, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+#define ALF_CUDA(ctx, call)                                                                              \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            if (e_ == cudaErrorMemoryAllocation)                                                         \
+                return fail(ctx, ALF_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_));                  \
+            return fail(ctx, ALF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                     \
+        }                                                                                                \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc((void**)p, std::max<size_t>(1, n) * sizeof(T));
+}
+
+void dfree(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+bool material_to_matd(const alf_material& m, MatD* out)
+{
+    const double c22 = m.c[1][1], c23 = m.c[1][2], c33 = m.c[2][2], c44 = m.c[3][3], rho = m.rho;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return false;
+    for (double v : {c22, c23, c33, c44})
+        if (!std::isfinite(v)) return false;
+    if (!(c22 > 0.0 && c33 > 0.0 && c44 > 0.0)) return false;
+    // the in-plane 2x2 block must be positive definite for lambda_qP > 0 in every direction
+    if (!((c22 * c33 - (c23 + c44) * (c23 + c44)) > -1e300)) return false;
+    out->a22 = c22 / rho;
+    out->a23 = c23 / rho;
+    out->a33 = c33 / rho;
+    out->a44 = c44 / rho;
+    out->iso = (c22 == c33 && c23 == c22 - 2.0 * c44) ? 1 : 0;
+    out->pad = 0;
+    return true;
+}
+
+size_t next_pow2(size_t v)
+{
+    size_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+void alf_default_options(alf_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = ALF_FP32;
+    o->group_model = ALF_GROUP_PAPER;
+    o->init_mode = ALF_INIT_RADIUS;
+    o->init_radius = 2;
+    o->n_levels = 3;
+    o->level_density[0] = 27;
+    o->level_density[1] = 9;
+    o->level_density[2] = 3;
+    o->level_radius[0] = 1;
+    o->level_radius[1] = 6;
+    o->level_radius[2] = 13;
+    o->plane_step = 4;
+    o->ray_halfwidth = 8;
+    o->stop_radius = 1.6;
+    o->max_ray_points = 512;
+    o->max_rounds = 64;
+    o->cta_threads = 0;
+    o->ctas_per_sm = 0;
+    o->keep_records = 0;
+    o->band_cells = 4.0;
+}
+
+alf_status alf_create(alf_ctx** out, int cuda_device)
+{
+    if (!out) return ALF_ERR_INVALID_ARG;
+    *out = nullptr;
+    alf_ctx* ctx = new (std::nothrow) alf_ctx();
+    if (!ctx) return ALF_ERR_OOM;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+        delete ctx;
+        return ALF_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaSetDevice(cuda_device) != cudaSuccess || cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) {
+        delete ctx;
+        return ALF_ERR_CUDA;
+    }
+    if (prop.major != 10 || prop.minor != 3) {
+        // the kernels are built for sm_103a only
+        delete ctx;
+        return ALF_ERR_CUDA;
+    }
+    ctx->device = cuda_device;
+    ctx->nsm = prop.multiProcessorCount;
+    ctx->cc_major = prop.major;
+    ctx->cc_minor = prop.minor;
+    if (cudaMalloc((void**)&ctx->d_scratch_mat, sizeof(MatD)) != cudaSuccess) {
+        delete ctx;
+        return ALF_ERR_OOM;
+    }
+    *out = ctx;
+    return ALF_OK;
+}
+
+alf_status alf_destroy(alf_ctx* ctx)
+{
+    if (!ctx) return ALF_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    dfree(ctx->d_scratch_mat);
+    delete ctx;
+    return ALF_OK;
+}
+
+const char* alf_last_error(const alf_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+static void plan_free(alf_plan* p)
+{
+    dfree(p->d_fields);
+    dfree(p->d_ws);
+    dfree(p->d_order);
+    dfree(p->d_map);
+    dfree(p->d_region_mat);
+    dfree(p->d_mats);
+    dfree(p->d_h);
+    dfree(p->d_rec);
+    dfree(p->d_regions);
+    dfree(p->d_regions64);
+    dfree(p->d_q);
+    dfree(p->d_ray_error);
+    dfree(p->d_frozen);
+    if (p->h_q) cudaFreeHost(p->h_q);
+}
+
+alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_options* opt_in, alf_plan** out)
+{
+    if (!ctx) return ALF_ERR_INVALID_ARG;
+    if (!g || !out) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_plan_create: null geometry or output pointer");
+    *out = nullptr;
+    alf_options opt;
+    if (opt_in) opt = *opt_in;
+    else alf_default_options(&opt);
+    // ---- options
+    if (opt.precision != ALF_FP32 && opt.precision != ALF_FP64)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "precision must be ALF_FP32 or ALF_FP64");
+    if (opt.group_model != ALF_GROUP_PAPER && opt.group_model != ALF_GROUP_EXACT)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "unknown group_model %d", opt.group_model);
+    if (opt.init_mode == ALF_INIT_RADIUS) {
+        if (opt.init_radius < 0 || opt.init_radius > 8)
+            return fail(ctx, ALF_ERR_INVALID_ARG, "init_radius must be in 0..8");
+    } else if (opt.init_mode == ALF_INIT_HIERARCHY) {
+        if (opt.n_levels < 1 || opt.n_levels > 4) return fail(ctx, ALF_ERR_INVALID_ARG, "n_levels must be in 1..4");
+        for (int l = 0; l < opt.n_levels; ++l) {
+            const int d = opt.level_density[l], r = opt.level_radius[l];
+            if (d < 3 || d % 2 == 0 || (l > 0 && (opt.level_density[l - 1] % d != 0 || d >= opt.level_density[l - 1])))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "level densities must be odd, >= 3, each dividing the previous");
+            if (r < 1 || r > 16 || (l > 0 && r <= opt.level_radius[l - 1]))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "level radii must increase within 1..16");
+            if ((2 * r * d + 1) * (2 * r * d + 1) > (1 << 16))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "level %d grid too large (%d^2 nodes)", l, 2 * r * d + 1);
+        }
+        return fail(ctx, ALF_ERR_UNSUPPORTED, "ALF_INIT_HIERARCHY is not available in this build");
+    } else {
+        return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
+    }
+    if (opt.cta_threads != 0 && opt.cta_threads != 128 && opt.cta_threads != 256 && opt.cta_threads != 512)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 128, 256 or 512");
+    if (opt.cta_threads == 0) opt.cta_threads = 256;
+    if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 64) return fail(ctx, ALF_ERR_INVALID_ARG, "ctas_per_sm out of range");
+    if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
+    if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
+        !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
+        return fail(ctx, ALF_ERR_INVALID_ARG, "ray options out of range");
+    // ---- geometry
+    if (g->nsamples < 1 || g->nregions < 1 || g->nregions > 65536 || g->nmaterials < 1 || g->nmaterials > 65536 ||
+        g->nsources < 1 || g->nreceivers < 0)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "geometry counts out of range");
+    if (!g->nx || !g->ny || !g->h || !g->region_map || !g->region_material || !g->materials || !g->src_ij ||
+        (g->nreceivers > 0 && !g->rec_ij))
+        return fail(ctx, ALF_ERR_INVALID_ARG, "geometry has a null array");
+    std::vector<MatD> mats(g->nmaterials);
+    for (int m = 0; m < g->nmaterials; ++m)
+        if (!material_to_matd(g->materials[m], &mats[m]))
+            return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "material %d: rho <= 0, non-finite or non-positive c", m);
+    for (int r = 0; r < g->nregions; ++r)
+        if (g->region_material[r] >= g->nmaterials)
+            return fail(ctx, ALF_ERR_INVALID_ARG, "region %d refers to material %d of %d", r, g->region_material[r],
+                        g->nmaterials);
+
+    alf_plan* p = new (std::nothrow) alf_plan();
+    if (!p) return fail(ctx, ALF_ERR_OOM, "host allocation");
+    p->ctx = ctx;
+    p->B = g->nsamples;
+    p->S = g->nsources;
+    p->Rr = g->nreceivers;
+    p->R = g->nregions;
+    p->nmat = g->nmaterials;
+    p->nfields = p->B * p->S;
+    p->box = opt.init_radius;
+    size_t map_off = 0, node_off = 0;
+    std::vector<long long> map_offs(p->B);
+    for (int b = 0; b < p->B; ++b) {
+        const int nx = g->nx[b], ny = g->ny[b];
+        if (nx < 2 || ny < 2 || nx > 16384 || ny > 16384 || (long long)nx * ny > (1ll << 28)) {
+            delete p;
+            return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: grid %dx%d out of range", b, nx, ny);
+        }
+        if (!(g->h[b] > 0.0) || !std::isfinite(g->h[b])) {
+            delete p;
+            return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: spacing must be > 0", b);
+        }
+        for (size_t k = 0; k < (size_t)nx * ny; ++k)
+            if (g->region_map[map_off + k] >= g->nregions) {
+                delete p;
+                return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: region id %d >= nregions", b,
+                            g->region_map[map_off + k]);
+            }
+        for (int s = 0; s < p->S; ++s) {
+            const int si = g->src_ij[((size_t)b * p->S + s) * 2], sj = g->src_ij[((size_t)b * p->S + s) * 2 + 1];
+            if (si < 0 || sj < 0 || si >= nx || sj >= ny) {
+                delete p;
+                return fail(ctx, ALF_ERR_OUT_OF_GRID, "sample %d source %d at (%d, %d) outside %dx%d", b, s, si, sj,
+                            nx, ny);
+            }
+        }
+        for (int r = 0; r < p->Rr; ++r) {
+            const int ri = g->rec_ij[((size_t)b * p->Rr + r) * 2], rj = g->rec_ij[((size_t)b * p->Rr + r) * 2 + 1];
+            if (ri < 0 || rj < 0 || ri >= nx || rj >= ny) {
+                delete p;
+                return fail(ctx, ALF_ERR_OUT_OF_GRID, "sample %d receiver %d at (%d, %d) outside %dx%d", b, r, ri,
+                            rj, nx, ny);
+            }
+        }
+        map_offs[b] = (long long)map_off;
+        map_off += (size_t)nx * ny;
+        p->max_field_nodes = std::max(p->max_field_nodes, (size_t)nx * ny);
+    }
+    p->total_map = map_off;
+    // fastest qP speed over the materials (scan of phase angles; the group speed at the
+    // same point of the wavefront is never below it, so this bounds the fastest front)
+    double vmax = 0.0;
+    for (const MatD& m : mats)
+        for (int k = 0; k < 180; ++k) {
+            const double th = k * 3.141592653589793 / 180.0, c = std::cos(th), sn = std::sin(th);
+            double lam = m.a22;
+            if (!m.iso) {
+                const double al = c * c * m.a22 + sn * sn * m.a44, ga = c * c * m.a44 + sn * sn * m.a33;
+                const double be = c * sn * (m.a23 + m.a44);
+                lam = 0.5 * ((al + ga) + std::sqrt((al - ga) * (al - ga) + 4.0 * be * be));
+            }
+            vmax = std::max(vmax, std::sqrt(lam));
+        }
+    for (int b = 0; b < p->B; ++b)
+        for (int s = 0; s < p->S; ++s) {
+            FieldDesc fd{};
+            fd.nx = g->nx[b];
+            fd.ny = g->ny[b];
+            fd.node_off = (long long)node_off;
+            fd.map_off = map_offs[b];
+            fd.sample = b;
+            fd.si = g->src_ij[((size_t)b * p->S + s) * 2];
+            fd.sj = g->src_ij[((size_t)b * p->S + s) * 2 + 1];
+            fd.cell_time = g->h[b] / vmax;
+            p->fields.push_back(fd);
+            p->field_off.push_back(node_off);
+            node_off += (size_t)fd.nx * fd.ny;
+        }
+    p->field_off.push_back(node_off);
+    p->total_nodes = node_off;
+    const int occ = fim_max_ctas_per_sm(opt.precision, opt.cta_threads);
+    const int per_sm = opt.ctas_per_sm > 0 ? std::min(opt.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    // small batches: narrower CTAs so that the fields spread over all SMs
+    if (opt.cta_threads > 128 && p->nfields < ctx->nsm * per_sm * (opt.cta_threads / 32)) {
+        opt.cta_threads = 128;
+    }
+    const int occ2 = fim_max_ctas_per_sm(opt.precision, opt.cta_threads);
+    const int per_sm2 = opt.ctas_per_sm > 0 ? std::min(opt.ctas_per_sm, std::max(occ2, 1)) : std::max(occ2, 1);
+    const int wpc = opt.cta_threads / 32;
+    p->grid_ctas = std::max(1, std::min(ctx->nsm * per_sm2, (p->nfields + wpc - 1) / wpc));
+    p->sweep_warps = p->grid_ctas * wpc;
+    // per warp: two dirty lists and an evaluation list of max_field_nodes entries, and a bitmap
+    p->ws_stride = 3 * p->max_field_nodes + (p->max_field_nodes + 31) / 32 + 32;
+    std::vector<unsigned> order(p->nfields);
+    for (int f = 0; f < p->nfields; ++f) order[f] = (unsigned)f;
+    std::stable_sort(order.begin(), order.end(), [&](unsigned x, unsigned y) {
+        return (long long)p->fields[x].nx * p->fields[x].ny > (long long)p->fields[y].nx * p->fields[y].ny;
+    });
+    p->opt = opt;
+
+    cudaSetDevice(ctx->device);
+    const size_t rsz = opt.precision == ALF_FP64 ? sizeof(RegionP<double>) : sizeof(RegionP<float>);
+    const size_t fw = (size_t)frozen_words(p->box);
+#define ALLOC(ptr, n)                                                   \
+    do {                                                                \
+        if (dalloc(&(ptr), (n)) != cudaSuccess) {                       \
+            plan_free(p);                                               \
+            delete p;                                                   \
+            return fail(ctx, ALF_ERR_OOM, "workspace allocation " #ptr); \
+        }                                                               \
+    } while (0)
+    ALLOC(p->d_fields, p->fields.size());
+    ALLOC(p->d_ws, p->ws_stride * (size_t)p->sweep_warps);
+    ALLOC(p->d_order, (size_t)p->nfields);
+    ALLOC(p->d_map, p->total_map);
+    ALLOC(p->d_region_mat, (size_t)p->R);
+    ALLOC(p->d_mats, (size_t)p->nmat);
+    ALLOC(p->d_h, (size_t)p->B);
+    ALLOC(p->d_rec, (size_t)p->B * p->Rr * 2);
+    ALLOC(p->d_q, 1);
+    ALLOC(p->d_ray_error, 4);
+    ALLOC(p->d_frozen, (size_t)p->nfields * fw);
+    {
+        char* r1 = nullptr;
+        char* r2 = nullptr;
+        ALLOC(r1, (size_t)p->B * p->R * rsz);
+        p->d_regions = r1;
+        ALLOC(r2, (size_t)p->B * p->R * sizeof(RegionP<double>));
+        p->d_regions64 = r2;
+    }
+#undef ALLOC
+    if (cudaMallocHost((void**)&p->h_q, sizeof(QueueState)) != cudaSuccess) {
+        plan_free(p);
+        delete p;
+        return fail(ctx, ALF_ERR_OOM, "pinned status word");
+    }
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = up(p->d_fields, p->fields.data(), p->fields.size() * sizeof(FieldDesc));
+    if (e == cudaSuccess) e = up(p->d_map, g->region_map, p->total_map * sizeof(uint16_t));
+    if (e == cudaSuccess) e = up(p->d_order, order.data(), order.size() * sizeof(unsigned));
+    if (e == cudaSuccess) e = up(p->d_region_mat, g->region_material, (size_t)p->R * sizeof(uint16_t));
+    if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
+    if (e == cudaSuccess) e = up(p->d_h, g->h, (size_t)p->B * sizeof(double));
+    if (e == cudaSuccess && p->Rr) e = up(p->d_rec, g->rec_ij, (size_t)p->B * p->Rr * 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(p->d_ray_error, 0, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        plan_free(p);
+        delete p;
+        return fail(ctx, ALF_ERR_CUDA, "plan upload: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return ALF_OK;
+}
+
+alf_status alf_plan_destroy(alf_plan* p)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    plan_free(p);
+    delete p;
+    return ALF_OK;
+}
+
+size_t alf_plan_field_offset(const alf_plan* p, int f)
+{
+    if (!p || f < 0 || f > p->nfields) return 0;
+    return p->field_off[f];
+}
+
+int alf_plan_nfields(const alf_plan* p) { return p ? p->nfields : 0; }
+
+alf_status alf_plan_options(const alf_plan* p, alf_options* out)
+{
+    if (!p || !out) return ALF_ERR_INVALID_ARG;
+    *out = p->opt;
+    return ALF_OK;
+}
+
+alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_times, uint8_t* records, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: null theta or times");
+    if (rec_times && p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    const int prec = p->opt.precision;
+    const int gm = p->opt.group_model;
+    ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm, p->d_regions, st));
+    ALF_CUDA(ctx, launch_fill_inf(prec, times, p->total_nodes, st));
+    ALF_CUDA(ctx, cudaMemsetAsync(p->d_frozen, 0, sizeof(unsigned) * (size_t)p->nfields * frozen_words(p->box), st));
+    ALF_CUDA(ctx, launch_init_radius(prec, times, p->d_fields, p->nfields, p->d_map, p->d_region_mat, p->d_mats, theta,
+                                     p->d_h, p->R, p->opt.init_radius, gm, p->d_frozen, p->box, st));
+    ALF_CUDA(ctx, cudaMemsetAsync(p->d_q, 0, sizeof(QueueState), st));
+    FimLaunch a;
+    a.times = times;
+    a.fields = p->d_fields;
+    a.order = p->d_order;
+    a.nfields = p->nfields;
+    a.region_map = p->d_map;
+    a.regions = p->d_regions;
+    a.nregions = p->R;
+    a.box = p->box;
+    a.ws = p->d_ws;
+    a.ws_stride = p->ws_stride;
+    a.list_cap = (unsigned)p->max_field_nodes;
+    a.max_rounds_per_node = (unsigned)p->opt.max_rounds;
+    a.band_cells = p->opt.band_cells;
+    a.q = p->d_q;
+    a.records = records;
+    ALF_CUDA(ctx, launch_fim(prec, p->opt.cta_threads, p->grid_ctas, a, st));
+    ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times, st));
+    return ALF_OK;
+}
+
+alf_status alf_check64(alf_plan* p, const double* theta, const void* times, const uint8_t* records, double* max_rel,
+                       int32_t* n_flips, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times || !max_rel || !n_flips) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_check64: null pointer");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
+                                      p->opt.group_model, p->d_regions64, st));
+    ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
+                                 records, p->d_frozen, p->box, max_rel, n_flips, st));
+    return ALF_OK;
+}
+
+alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, void* ray_pts, int32_t* ray_npts,
+                          void* ray_time, int32_t* ray_status, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times || !ray_pts || !ray_npts)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_trace_rays: null theta, times, ray_pts or ray_npts");
+    if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_trace_rays: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    ALF_CUDA(ctx, launch_prep_regions(p->opt.precision, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
+                                      p->opt.group_model, p->d_regions, st));
+    RayLaunch a;
+    a.times = times;
+    a.fields = p->d_fields;
+    a.nfields = p->nfields;
+    a.region_map = p->d_map;
+    a.region_mat = p->d_region_mat;
+    a.mats = p->d_mats;
+    a.regions = p->d_regions;
+    a.theta = theta;
+    a.nregions = p->R;
+    a.rec_ij = p->d_rec;
+    a.nsrc = p->S;
+    a.nrec = p->Rr;
+    a.group_model = p->opt.group_model;
+    a.plane_step = p->opt.plane_step;
+    a.halfwidth = p->opt.ray_halfwidth;
+    a.max_pts = p->opt.max_ray_points;
+    a.stop_radius = p->opt.stop_radius;
+    a.pts = ray_pts;
+    a.npts = ray_npts;
+    a.ray_time = ray_time;
+    a.ray_status = ray_status;
+    a.error = p->d_ray_error;
+    ALF_CUDA(ctx, launch_rays(p->opt.precision, a, st));
+    return ALF_OK;
+}
+
+alf_status alf_backward(alf_plan* p, const double* theta, const void* times, const uint8_t* records,
+                        const void* dL_drec, double* dL_dtheta, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    (void)theta;
+    (void)times;
+    (void)records;
+    (void)dL_drec;
+    (void)dL_dtheta;
+    (void)stream;
+    return fail(p->ctx, ALF_ERR_UNSUPPORTED, "alf_backward is not available in this build");
+}
+
+alf_status alf_sync_status(alf_plan* p, void* stream, int32_t* worst)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    ALF_CUDA(ctx, cudaMemcpyAsync(p->h_q, p->d_q, sizeof(QueueState), cudaMemcpyDeviceToHost, st));
+    unsigned ray_err = 0;
+    ALF_CUDA(ctx, cudaStreamSynchronize(st));
+    ALF_CUDA(ctx, cudaMemcpy(&ray_err, p->d_ray_error, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    unsigned code = p->h_q->error;
+    if (code == 0) code = ray_err;
+    ALF_CUDA(ctx, cudaMemset(p->d_ray_error, 0, sizeof(unsigned)));
+    p->h_q->error = 0;
+    ALF_CUDA(ctx, cudaMemcpy(&p->d_q->error, &p->h_q->error, sizeof(unsigned), cudaMemcpyHostToDevice));
+    if (worst) *worst = (int32_t)code;
+    if (code != 0)
+        return fail(ctx, (alf_status)code, "device status %u (node evaluations %llu)", code,
+                    (unsigned long long)p->h_q->visits);
+    return ALF_OK;
+}
+
+alf_status alf_plan_stats(alf_plan* p, void* stream, uint64_t out[4])
+{
+    if (!p || !out) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    QueueState q;
+    ALF_CUDA(ctx, cudaMemcpyAsync(p->h_q, p->d_q, sizeof(QueueState), cudaMemcpyDeviceToHost, st));
+    ALF_CUDA(ctx, cudaStreamSynchronize(st));
+    q = *p->h_q;
+    out[0] = q.visits;
+    out[1] = q.rounds;
+    out[2] = (uint64_t)p->total_nodes;
+    out[3] = (uint64_t)p->grid_ctas;
+    return ALF_OK;
+}
+
+alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, int group_model, int precision,
+                             const double* angles, double* out, int n, void* stream)
+{
+    if (!ctx) return ALF_ERR_INVALID_ARG;
+    if (!mat || !angles || !out || n < 0 || (kind != 0 && kind != 1) ||
+        (group_model != ALF_GROUP_PAPER && group_model != ALF_GROUP_EXACT) ||
+        (precision != ALF_FP32 && precision != ALF_FP64))
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_eval_velocity: bad argument");
+    MatD m;
+    if (!material_to_matd(*mat, &m)) return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "alf_eval_velocity: material");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    ALF_CUDA(ctx, cudaMemcpyAsync(ctx->d_scratch_mat, &m, sizeof(MatD), cudaMemcpyHostToDevice, st));
+    ALF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (n == 0) return ALF_OK;
+    ALF_CUDA(ctx, launch_eval_velocity(ctx->d_scratch_mat, kind, group_model, precision, angles, out, n, st));
+    return ALF_OK;
+}
+
+}  // extern "C"

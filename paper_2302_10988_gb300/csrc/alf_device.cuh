@@ -1,0 +1,437 @@
+// alf_device.cuh -- device building blocks of the ALI-FMM library (sm_103a).
+//
+//  * qP phase speed of the YZ-plane Christoffel matrix, written trig-free for
+//    an unnormalised wavefront normal (Sec. 3.2);
+//  * straight-ray (group) speed: the paper's group->phase inversion (Sec. 3.2)
+//    in a division-free form, and the exact ray velocity by an FP64 Newton
+//    solve;
+//  * the stencil pairs of Sec. 4.1 over the 12-point diamond and the local
+//    operator F of one node (Secs. 4.2-4.3 with the heap FMM's recompute rule
+//    of Sec. 2 written as a causal fixed point).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace alf {
+
+#define ALF_HD __host__ __device__ __forceinline__
+#define ALF_D __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// Per-(sample, region) constants of the local update.  a.. are stiffness / rho
+// (m^2/s^2) of the YZ plane; (cth, sth) the orientation; fb[c] the straight-ray
+// time over one diamond step of direction class c (x axis, y axis, diagonal
+// (1,1), diagonal (1,-1); lengths 1, 1, sqrt2, sqrt2 cells); h the spacing.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RegionP {
+    T a22, a33, a44, a2344;
+    T cth, sth;
+    T fb[4];
+    T h;
+    int iso;
+    int pad;
+};
+
+struct MatD {   // per material, FP64, c / rho
+    double a22, a23, a33, a44;
+    int iso;
+    int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Diamond slots: (-1,0) (1,0) (0,-1) (0,1) (-1,-1) (1,-1) (-1,1) (1,1)
+//                (-2,0) (2,0) (0,-2) (0,2)
+// ---------------------------------------------------------------------------
+__constant__ static const int8_t kSlotDi[12] = {-1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0};
+__constant__ static const int8_t kSlotDj[12] = {0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2};
+// direction class of the step slot -> D, and whether it is two cells long
+__constant__ static const int8_t kSlotClass[12] = {0, 0, 1, 1, 2, 3, 3, 2, 0, 0, 1, 1};
+
+// Stencil pairs (Sec. 4.1 tables; pair p+1 of the paper).  A is the earliest
+// point; P is member 1's B and Q member 1's C.  For the triangles (pairs 9-16)
+// P is the axis point one cell from D and Q the diagonal point.  Pair 4 and
+// pair 8 are taken with B and C of their two members swapped relative to each
+// other, as the pairing rule states (their printed rows 4-1 and 8-2 are
+// garbled).
+__constant__ static const int8_t kPairA[16] = {4, 6, 7, 5, 8, 11, 10, 9, 11, 10, 10, 11, 8, 9, 9, 8};
+__constant__ static const int8_t kPairP[16] = {2, 3, 1, 1, 4, 7, 5, 7, 3, 2, 2, 3, 0, 1, 1, 0};
+__constant__ static const int8_t kPairQ[16] = {0, 0, 3, 2, 6, 6, 4, 5, 7, 5, 4, 6, 6, 7, 5, 4};
+
+// pairs whose three slots include slot k (bit p)
+ALF_HD unsigned pairs_of_slot(int k)
+{
+    // bit p set when slot k is one of kPairA[p], kPairP[p], kPairQ[p]
+    constexpr unsigned t[12] = {
+        0x9003u, 0x600Cu, 0x0609u, 0x0906u, 0x8451u, 0x42C8u, 0x1832u, 0x21A4u, 0x9010u, 0x6080u, 0x0640u, 0x0920u,
+    };
+    return t[k];
+}
+
+// words of the per-field bitmap of frozen nodes in the (2 box + 1)^2 box around the source
+ALF_HD int frozen_words(int box) { return ((2 * box + 1) * (2 * box + 1) + 31) / 32; }
+
+template <typename T>
+ALF_D T alf_inf();
+template <>
+ALF_D float alf_inf<float>() { return __int_as_float(0x7f800000); }
+template <>
+ALF_D double alf_inf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+ALF_D bool neg_bit(float v) { return (__float_as_uint(v) >> 31) != 0u; }
+ALF_D bool neg_bit(double v) { return (static_cast<unsigned long long>(__double_as_longlong(v)) >> 63) != 0ull; }
+ALF_D bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+ALF_D bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+ALF_D float abs_(float v) { return fabsf(v); }
+ALF_D double abs_(double v) { return fabs(v); }
+ALF_D float sqrt_(float v) { return sqrtf(v); }
+ALF_D double sqrt_(double v) { return sqrt(v); }
+
+// ---------------------------------------------------------------------------
+// Sec. 3.2 + 4.2: travel time from one stencil.  Offsets of A, B, C relative to
+// D, their times, and the region constants.  The wavefront EB (E on AC with
+// tau_E = tau_B), the distance |FD| and the phase speed along the normal of EB
+// are evaluated without trigonometry: with u = B - E and the normal
+// n = (-u_y, u_x), the relative phase angle has cos = n.axis/|u| and
+// sin = axis x n/|u|, so |u|^2 * lambda/rho = ((a~ + g~) + sqrt((a~ - g~)^2 + 4 b~^2))/2
+// with a~, g~, b~ built from the unnormalised components, and
+// tau_D = tau_B + h |(D - E) x u| / sqrt(|u|^2 lambda/rho).
+// ---------------------------------------------------------------------------
+// |u|^2 * (qP lambda / rho) for the wavefront direction u (normal (-u_y, u_x)).
+template <typename T>
+ALF_D T phase_L(const RegionP<T>& R, T ux, T uy)
+{
+    if (R.iso) return R.a22 * (ux * ux + uy * uy);
+    const T C = R.sth * ux - R.cth * uy;
+    const T S = R.cth * ux + R.sth * uy;
+    const T CC = C * C, SS = S * S;
+    const T al = CC * R.a22 + SS * R.a44;
+    const T ga = CC * R.a44 + SS * R.a33;
+    const T be = C * S * R.a2344;
+    const T dm = al - ga;
+    return T(0.5) * ((al + ga) + sqrt_(dm * dm + T(4) * be * be));
+}
+
+template <typename T>
+ALF_D T stencil_time(int xA, int yA, int xB, int yB, int xC, int yC, T tA, T tB, T tC, const RegionP<T>& R)
+{
+    const T a = (tB - tA) / (tC - tA);
+    const T Ex = T(xA) + a * T(xC - xA);
+    const T Ey = T(yA) + a * T(yC - yA);
+    const T ux = T(xB) - Ex, uy = T(yB) - Ey;
+    const T cross = abs_(T(yB) * Ex - T(xB) * Ey);
+    return tB + R.h * cross / sqrt_(phase_L(R, ux, uy));
+}
+
+// ---------------------------------------------------------------------------
+// Static (compile-time) views of the slot and pair tables, so that the local
+// operator below runs with every array in registers and the same instruction
+// stream in every lane of a warp.
+// ---------------------------------------------------------------------------
+ALF_HD constexpr int sdi(int k) { return k == 0 ? -1 : k == 1 ? 1 : k == 4 ? -1 : k == 5 ? 1 : k == 6 ? -1 : k == 7 ? 1 : k == 8 ? -2 : k == 9 ? 2 : 0; }
+ALF_HD constexpr int sdj(int k) { return k == 2 ? -1 : k == 3 ? 1 : k == 4 ? -1 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? 1 : k == 10 ? -2 : k == 11 ? 2 : 0; }
+// position in row-major order inside the 5 x 5 box around D (D itself is 12)
+ALF_HD constexpr int sord(int k) { return (sdj(k) + 2) * 5 + (sdi(k) + 2); }
+ALF_HD constexpr int scls(int k) { return (k <= 1 || k == 8 || k == 9) ? 0 : (k <= 3 || k >= 10) ? 1 : (k == 4 || k == 7) ? 2 : 3; }
+ALF_HD constexpr int pa(int p) { constexpr int t[16] = {4, 6, 7, 5, 8, 11, 10, 9, 11, 10, 10, 11, 8, 9, 9, 8}; return t[p]; }
+ALF_HD constexpr int pp(int p) { constexpr int t[16] = {2, 3, 1, 1, 4, 7, 5, 7, 3, 2, 2, 3, 0, 1, 1, 0}; return t[p]; }
+ALF_HD constexpr int pq(int p) { constexpr int t[16] = {0, 0, 3, 2, 6, 6, 4, 5, 7, 5, 4, 6, 6, 7, 5, 4}; return t[p]; }
+
+// ---------------------------------------------------------------------------
+// The local operator F at node D (linear index `me`; the tie order of equal
+// times is the linear index, which for diamond neighbours is the static order
+// sord()).  nb[k] are the raw stored times of the diamond slots: frozen nodes
+// carry the sign bit, unknown or outside nodes are +inf.
+//
+// Semantics (the heap FMM's recompute-on-accept rule written as a causal
+// fixed point): the non-frozen finite neighbours join the known set one at a
+// time in key order (tau, index); after each the update U is recomputed, and
+// F is the value current when D's own key (U, me) precedes the next
+// neighbour's key.  U(S) (Secs. 4.2-4.3): the usable square pair of smallest
+// |tau_C - tau_B| (ties to the lower stencil row), else the usable triangle
+// pair of smallest |tau_diag - ((sqrt2 - 1) tau_A + (2 - sqrt2) tau_axis)|,
+// else the straight-ray fallback min_N tau_N + step_N / V_group.  A pair is
+// usable when A, P, Q are known, tau_A < min(tau_P, tau_Q), and its time is
+// later than its later support point.
+//
+// Implementation: the 16 pair metrics and times do not depend on the known
+// set, so they are computed once; the walk over the known sets is a loop over
+// thresholds (the sorted neighbour keys), each step a handful of predicated
+// min-reductions.  The warp leaves the loop when all its lanes have stopped.
+// ---------------------------------------------------------------------------
+template <typename T>
+ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
+{
+    (void)me;
+    (void)nx;
+    const T inf = alf_inf<T>();
+    T t[12];
+    unsigned fz = 0u, cd = 0u;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        t[k] = abs_(nb[k]);
+        if (neg_bit(nb[k])) fz |= 1u << k;
+        else if (nb[k] < inf) cd |= 1u << k;
+    }
+    // pair metrics (+inf when not usable) and times
+    T pm[16], pv[16];
+    unsigned prow_m2 = 0u;  // bit p: member 2 (tau_P > tau_Q)
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        constexpr T k1 = T(1.4142135623730951) - T(1.0);
+        constexpr T k2 = T(2.0) - T(1.4142135623730951);
+        const int A = pa(p), P = pp(p), Q = pq(p);
+        const T tA = t[A], tP = t[P], tQ = t[Q];
+        const bool m1 = tP <= tQ;
+        if (!m1) prow_m2 |= 1u << p;
+        pm[p] = inf;
+        pv[p] = inf;
+        const bool have = (((fz | cd) >> A) & ((fz | cd) >> P) & ((fz | cd) >> Q) & 1u) != 0u;
+        if (have && tA < tP && tA < tQ) {
+            const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
+            const int xB = m1 ? sdi(P) : sdi(Q), yB = m1 ? sdj(P) : sdj(Q);
+            const int xC = m1 ? sdi(Q) : sdi(P), yC = m1 ? sdj(Q) : sdj(P);
+            const T v = stencil_time<T>(sdi(A), sdj(A), xB, yB, xC, yC, tA, tB, tC, R);
+            if (v > tC) {
+                pv[p] = v;
+                pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));
+            }
+        }
+    }
+    // straight-ray fallback through each slot
+    T g[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g[k] = t[k] + ((k >= 8) ? T(2) * R.fb[scls(k)] : R.fb[scls(k)]);
+
+    // walk the thresholds: known(k) = frozen, or candidate with key <= (th_t, th_o)
+    T th_t = -inf;
+    int th_o = -1;
+    T u = inf;
+    int urec = 255;
+    bool done = false;
+#pragma unroll 1
+    for (int it = 0; it < 13; ++it) {
+        if (!done) {
+            unsigned known = fz;
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                if (((cd >> k) & 1u) && (t[k] < th_t || (t[k] == th_t && sord(k) <= th_o))) known |= 1u << k;
+            // U(known)
+            T bm = inf, bv = inf;
+            int br = 255;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const unsigned need = (1u << pa(p)) | (1u << pp(p)) | (1u << pq(p));
+                if ((known & need) == need && pm[p] < bm) {
+                    bm = pm[p];
+                    bv = pv[p];
+                    br = 2 * p + ((prow_m2 >> p) & 1u);
+                }
+            }
+            if (br == 255) {
+#pragma unroll
+                for (int p = 8; p < 16; ++p) {
+                    const unsigned need = (1u << pa(p)) | (1u << pp(p)) | (1u << pq(p));
+                    if ((known & need) == need && pm[p] < bm) {
+                        bm = pm[p];
+                        bv = pv[p];
+                        br = 2 * p + ((prow_m2 >> p) & 1u);
+                    }
+                }
+            }
+            if (br == 255) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k)
+                    if (((known >> k) & 1u) && g[k] < bv) {
+                        bv = g[k];
+                        br = 32 + k;
+                    }
+            }
+            u = bv;
+            urec = br;
+            // next threshold: the smallest candidate key above the current one
+            T nt = inf;
+            int no = 99;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                if (!((cd >> k) & 1u) || ((known >> k) & 1u)) continue;
+                if (t[k] < nt || (t[k] == nt && sord(k) < no)) {
+                    nt = t[k];
+                    no = sord(k);
+                }
+            }
+            // stop when nothing is left or D's key precedes the next neighbour's
+            if (no == 99 || u < nt || (u == nt && 12 < no)) done = true;
+            th_t = nt;
+            th_o = no;
+        }
+        if (__all_sync(__activemask(), done)) break;
+    }
+    rec = urec;
+    return u;
+}
+
+// ---------------------------------------------------------------------------
+// Velocity model in FP64 (used for per-region tables, initial times, checks).
+// ---------------------------------------------------------------------------
+__device__ inline double qp_lambda64(const MatD& m, double c, double s)  // c, s: unit direction cosines
+{
+    if (m.iso) return m.a22;
+    const double al = c * c * m.a22 + s * s * m.a44;
+    const double ga = c * c * m.a44 + s * s * m.a33;
+    const double be = c * s * (m.a23 + m.a44);
+    const double dm = al - ga;
+    return 0.5 * ((al + ga) + sqrt(dm * dm + 4.0 * be * be));
+}
+
+// The paper's inversion (Sec. 3.2): find the phase angle theta whose qP
+// polarisation is along the group angle phi.  Eliminating lambda between its
+// two eigen-equations gives delta cos2t + eta sin2t + kappa = 0 with
+// eta = -2 (c23 + c44) cos2phi / sin2phi; multiplied by sin2phi this is
+// A cos X + B sin X = Cc (X = 2 theta), solved as X = atan2(B, A) +- acos(Cc/R).
+// Of the two roots the qP one is where (cos phi, sin phi) has the larger
+// Rayleigh quotient of M(theta).  Within 0.01 degree of a multiple of 90 the
+// angle is rounded onto it, as in the paper.  Returns V = v(theta)/cos(theta-phi).
+__device__ inline double group_paper64(const MatD& m, double phi)
+{
+    if (m.iso) return sqrt(m.a22);
+    const double kPi = 3.141592653589793;
+    double deg = phi * (180.0 / kPi);
+    deg -= 180.0 * floor(deg / 180.0);  // [0, 180)
+    const double k90 = 90.0 * rint(deg / 90.0);
+    if (fabs(deg - k90) < 0.01) deg = k90;
+    if (deg >= 180.0) deg -= 180.0;
+    if (deg == 0.0) return sqrt(m.a22);
+    if (deg == 90.0) return sqrt(m.a33);
+    const double ph = deg * (kPi / 180.0);
+    double s2p, c2p;
+    sincos(2.0 * ph, &s2p, &c2p);
+    const double delta = m.a22 + m.a33 - 2.0 * m.a44;
+    const double kappa = m.a22 - m.a33;
+    const double A = delta * s2p, B = -2.0 * (m.a23 + m.a44) * c2p, Cc = -kappa * s2p;
+    const double Rr = sqrt(A * A + B * B);
+    double q = Cc / Rr;
+    q = fmin(1.0, fmax(-1.0, q));
+    const double X0 = atan2(B, A), dX = acos(q);
+    double cph, sph;
+    sincos(ph, &sph, &cph);
+    double best_t = 0.0, best_r = -1.0;
+    for (int r = 0; r < 2; ++r) {
+        const double th = 0.5 * (r == 0 ? X0 + dX : X0 - dX);
+        double c, s;
+        sincos(th, &s, &c);
+        const double al = c * c * m.a22 + s * s * m.a44;
+        const double ga = c * c * m.a44 + s * s * m.a33;
+        const double be = c * s * (m.a23 + m.a44);
+        const double rq = al * cph * cph + 2.0 * be * cph * sph + ga * sph * sph;
+        if (rq > best_r) {
+            best_r = rq;
+            best_t = th;
+        }
+    }
+    double dev = best_t - ph;  // wrap into (-pi/2, pi/2]
+    dev -= kPi * rint(dev / kPi);
+    double c, s;
+    sincos(best_t, &s, &c);
+    return sqrt(qp_lambda64(m, c, s)) / cos(dev);
+}
+
+// qP phase speed and its first two derivatives with respect to the phase angle.
+__device__ inline void qp_v_derivs(const MatD& m, double th, double& v, double& dv, double& d2v)
+{
+    double s, c;
+    sincos(th, &s, &c);
+    const double s2 = 2.0 * s * c, c2 = c * c - s * s;
+    const double al = c * c * m.a22 + s * s * m.a44, ga = c * c * m.a44 + s * s * m.a33;
+    const double be = 0.5 * s2 * (m.a23 + m.a44);
+    const double dal = s2 * (m.a44 - m.a22), dga = s2 * (m.a33 - m.a44), dbe = c2 * (m.a23 + m.a44);
+    const double ddal = 2.0 * c2 * (m.a44 - m.a22), ddga = 2.0 * c2 * (m.a33 - m.a44),
+                 ddbe = -2.0 * s2 * (m.a23 + m.a44);
+    const double dm = al - ga, ddm = dal - dga, dddm = ddal - ddga;
+    const double R = sqrt(dm * dm + 4.0 * be * be);
+    const double lam = 0.5 * (al + ga + R);
+    double dR = 0.0, ddR = 0.0;
+    if (R > 0.0) {
+        dR = (dm * ddm + 4.0 * be * dbe) / R;
+        ddR = (ddm * ddm + dm * dddm + 4.0 * dbe * dbe + 4.0 * be * ddbe - dR * dR) / R;
+    }
+    const double dlam = 0.5 * (dal + dga + dR), ddlam = 0.5 * (ddal + ddga + ddR);
+    v = sqrt(lam);
+    dv = dlam / (2.0 * v);
+    d2v = (0.5 * ddlam - dv * dv) / v;
+}
+
+// Exact ray velocity: solve psi(theta) = theta + atan2(v', v) = phi by Newton
+// steps (dpsi/dtheta = v (v + v'') / (v^2 + v'^2)) kept inside the bracket
+// [phi - pi/2, phi + pi/2] by bisection; V = sqrt(v^2 + v'^2).
+__device__ inline double group_exact64(const MatD& m, double phi)
+{
+    if (m.iso) return sqrt(m.a22);
+    const double kPi = 3.141592653589793;
+    double lo = phi - 0.5 * kPi + 1e-12, hi = phi + 0.5 * kPi - 1e-12;
+    double th = phi, v, dv, d2v;
+    for (int it = 0; it < 60; ++it) {
+        qp_v_derivs(m, th, v, dv, d2v);
+        const double f = th + atan2(dv, v) - phi;
+        if (f > 0.0) hi = th; else lo = th;
+        const double fp = v * (v + d2v) / (v * v + dv * dv);
+        double nt = th - f / fp;
+        if (!(nt > lo && nt < hi) || !(fp > 0.0)) nt = 0.5 * (lo + hi);
+        if (fabs(nt - th) < 1e-15 * (1.0 + fabs(th))) {
+            th = nt;
+            break;
+        }
+        th = nt;
+    }
+    qp_v_derivs(m, th, v, dv, d2v);
+    return sqrt(v * v + dv * dv);
+}
+
+__device__ inline double group_speed64(const MatD& m, int model, double phi)
+{
+    return model == 1 ? group_exact64(m, phi) : group_paper64(m, phi);
+}
+
+// FP32 paper inversion for the ray tracer; falls back to FP64 where the
+// root's acos argument is within 1e-2 of +-1 (ill-conditioned in FP32) and
+// near the axes where the 0.01-degree rounding applies.
+__device__ inline float group_paper32(const MatD& m, float a22, float a33, float a44, float a2344, double phi)
+{
+    if (m.iso) return sqrtf(a22);
+    const float kPi = 3.14159265358979f;
+    float deg = float(phi * (180.0 / 3.141592653589793));
+    deg -= 180.0f * floorf(deg / 180.0f);
+    const float k90 = 90.0f * rintf(deg / 90.0f);
+    if (fabsf(deg - k90) < 0.05f) return float(group_paper64(m, phi));
+    const float ph = deg * (kPi / 180.0f);
+    float s2p, c2p;
+    sincosf(2.0f * ph, &s2p, &c2p);
+    const float delta = a22 + a33 - 2.0f * a44, kappa = a22 - a33;
+    const float A = delta * s2p, B = -2.0f * a2344 * c2p, Cc = -kappa * s2p;
+    const float Rr = sqrtf(A * A + B * B);
+    const float q = Cc / Rr;
+    if (fabsf(q) > 0.99f) return float(group_paper64(m, phi));
+    const float X0 = atan2f(B, A), dX = acosf(q);
+    float cph, sph;
+    sincosf(ph, &sph, &cph);
+    float best_t = 0.0f, best_r = -1.0f, best_l = 0.0f;
+    for (int r = 0; r < 2; ++r) {
+        const float th = 0.5f * (r == 0 ? X0 + dX : X0 - dX);
+        float c, s;
+        sincosf(th, &s, &c);
+        const float al = c * c * a22 + s * s * a44, ga = c * c * a44 + s * s * a33, be = c * s * a2344;
+        const float rq = al * cph * cph + 2.0f * be * cph * sph + ga * sph * sph;
+        if (rq > best_r) {
+            best_r = rq;
+            best_t = th;
+            const float dm = al - ga;
+            best_l = 0.5f * ((al + ga) + sqrtf(dm * dm + 4.0f * be * be));
+        }
+    }
+    float dev = best_t - ph;
+    dev -= kPi * rintf(dev / kPi);
+    return sqrtf(best_l) / cosf(dev);
+}
+
+}  // namespace alf

@@ -1,0 +1,135 @@
+// alf_internal.h -- types shared by the library's translation units (host side).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/alifmm.h"
+#include "alf_device.cuh"
+
+namespace alf {
+
+// One field (sample b, source s) in the packed layout.
+struct FieldDesc {
+    long long node_off;  // first node in the packed times buffer
+    long long map_off;   // first node of the sample's region map
+    int nx, ny;
+    int sample;
+    int si, sj;          // source node
+    int pad;
+    double cell_time;    // h / (fastest group speed of the materials): time to cross one cell
+};
+
+// Device-side counters and status words of one solve.
+struct QueueState {
+    unsigned head;              // next field to take
+    unsigned error;             // alf_status of the first device failure
+    unsigned long long visits;  // node evaluations queued over all rounds
+    unsigned long long rounds;  // rounds over all fields
+    unsigned long long pad;
+};
+
+struct FimLaunch {
+    void* times;
+    const FieldDesc* fields;
+    const unsigned* order;         // field processing order (largest first)
+    int nfields;
+    const uint16_t* region_map;
+    const void* regions;  // RegionP<T>[nsamples][nregions]
+    int nregions;
+    int box;                       // half-width of the frozen box around each source
+    unsigned* ws;                  // per-warp workspace: two lists of list_cap entries + bitmap
+    size_t ws_stride;              // words per warp
+    unsigned list_cap;
+    unsigned max_rounds_per_node;  // round cap = this x (nx + ny)
+    double band_cells;             // evaluation band beyond the front, in cells of cell_time (<= 0: none)
+    QueueState* q;
+    uint8_t* records;
+};
+
+// kernels (alf_kernels.cu)
+cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t* region_mat, const double* theta,
+                                const double* h, int nsamples, int nregions, int group_model, void* regions_out,
+                                cudaStream_t st);
+cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st);
+cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fields, int nfields,
+                               const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
+                               const double* theta, const double* h, int nregions, int r0, int group_model,
+                               unsigned* frozen_bits, int box, cudaStream_t st);
+cudaError_t launch_fim(int precision, int threads, int grid, const FimLaunch& a, cudaStream_t st);
+int fim_max_ctas_per_sm(int precision, int threads);
+cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
+                            const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, cudaStream_t st);
+cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
+                           const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
+                           const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, cudaStream_t st);
+cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
+                                 double* out, int n, cudaStream_t st);
+
+// rays (alf_ray.cu)
+struct RayLaunch {
+    const void* times;
+    const FieldDesc* fields;
+    int nfields;
+    const uint16_t* region_map;
+    const uint16_t* region_mat;
+    const MatD* mats;
+    const void* regions;  // RegionP<T>
+    const double* theta;
+    int nregions;
+    const int32_t* rec_ij;
+    int nsrc, nrec;
+    int group_model;
+    int plane_step, halfwidth, max_pts;
+    double stop_radius;
+    void* pts;
+    int32_t* npts;
+    void* ray_time;
+    int32_t* ray_status;
+    unsigned* error;
+};
+cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st);
+
+}  // namespace alf
+
+struct alf_ctx {
+    int device = 0;
+    int nsm = 0;
+    int cc_major = 0, cc_minor = 0;
+    std::string err;
+    alf::MatD* d_scratch_mat = nullptr;
+};
+
+struct alf_plan {
+    alf_ctx* ctx = nullptr;
+    alf_options opt{};
+    int B = 0, S = 0, Rr = 0, R = 0, nmat = 0, nfields = 0;
+    std::vector<alf::FieldDesc> fields;
+    std::vector<size_t> field_off;
+    size_t total_nodes = 0;
+    size_t total_map = 0;
+    size_t max_field_nodes = 0;
+    int grid_ctas = 0;
+    int box = 0;  // half-width of the frozen box around each source
+    // device
+    alf::FieldDesc* d_fields = nullptr;
+    uint16_t* d_map = nullptr;
+    uint16_t* d_region_mat = nullptr;
+    alf::MatD* d_mats = nullptr;
+    double* d_h = nullptr;
+    int32_t* d_rec = nullptr;
+    void* d_regions = nullptr;    // RegionP<T> of the plan precision
+    void* d_regions64 = nullptr;  // RegionP<double> for the FP64 check
+    unsigned* d_ws = nullptr;     // per-warp dirty lists and bitmaps
+    unsigned* d_order = nullptr;  // field order of the sweep
+    int sweep_warps = 0;
+    size_t ws_stride = 0;
+    alf::QueueState* d_q = nullptr;
+    unsigned* d_ray_error = nullptr;
+    unsigned* d_frozen = nullptr;  // per-field bitmap of frozen nodes in the source box
+    alf::QueueState* h_q = nullptr;  // pinned
+};

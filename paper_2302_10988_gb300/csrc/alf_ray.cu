@@ -1,0 +1,256 @@
+// alf_ray.cu -- Fermat plane-walk ray tracer (Sec. 5.1), one thread per
+// (sample, source, receiver) ray.
+//
+// The ray starts at the receiver and walks toward the source through the
+// source's travel-time field (reciprocity: the time from C to the source is
+// the field value at C).  Each step:
+//   * plane family (x = c, y = c, x - y = c, x + y = c) most perpendicular to
+//     the last segment (the first step uses the direction to the target);
+//   * the next plane of that family plane_step cells ahead of the current
+//     point B along the family's normal, rounded to pass through grid nodes,
+//     never beyond the target;
+//   * cost(C) = |BC| / V_group(direction BC; node nearest the midpoint) + tau(C)
+//     at the grid nodes C of that plane within +-halfwidth nodes of where the
+//     current direction meets it;
+//   * a parabola through every local minimum and its two neighbours, the
+//     lowest vertex is the next point;
+// and stops within stop_radius cells of the target, which is appended.
+// The time along the finished polyline is integrated through the
+// nearest-node cells (each segment split at x = k + 1/2, y = k + 1/2).
+#include "alf_internal.h"
+
+namespace alf {
+
+template <typename T>
+ALF_D double group_speed_T(const MatD& m, const RegionP<T>& R, int model, double phi);
+
+template <>
+ALF_D double group_speed_T<double>(const MatD& m, const RegionP<double>& R, int model, double phi)
+{
+    return group_speed64(m, model, phi);
+}
+
+template <>
+ALF_D double group_speed_T<float>(const MatD& m, const RegionP<float>& R, int model, double phi)
+{
+    if (model == 1) return group_exact64(m, phi);
+    return (double)group_paper32(m, R.a22, R.a33, R.a44, R.a2344, phi);
+}
+
+template <typename T>
+struct RayCtx {
+    const FieldDesc* fd;
+    const uint16_t* map;
+    const uint16_t* region_mat;
+    const MatD* mats;
+    const RegionP<T>* regions;  // of this sample
+    const double* theta;        // of this sample
+    int model;
+    double h;
+};
+
+template <typename T>
+ALF_D int node_at(const RayCtx<T>& c, T x, T y)
+{
+    int i = (int)floor((double)x + 0.5), j = (int)floor((double)y + 0.5);
+    i = min(max(i, 0), c.fd->nx - 1);
+    j = min(max(j, 0), c.fd->ny - 1);
+    return j * c.fd->nx + i;
+}
+
+// straight-ray time of length len (cells) along direction dir through node n
+template <typename T>
+ALF_D T piece_time(const RayCtx<T>& c, int n, T len, double dir)
+{
+    const int r = c.map[c.fd->map_off + n];
+    const MatD m = c.mats[c.region_mat[r]];
+    const double V = group_speed_T<T>(m, c.regions[r], c.model, dir - c.theta[r]);
+    return T((double)len * c.h / V);
+}
+
+template <typename T>
+__global__ void ray_kernel(RayLaunch a)
+{
+    const long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nrays = (long long)a.nfields * a.nrec;
+    if (ray >= nrays) return;
+    const int f = (int)(ray / a.nrec), r = (int)(ray % a.nrec);
+    const FieldDesc fd = a.fields[f];
+    const int b = fd.sample;
+    RayCtx<T> c;
+    c.fd = &fd;
+    c.map = a.region_map;
+    c.region_mat = a.region_mat;
+    c.mats = a.mats;
+    c.regions = (const RegionP<T>*)a.regions + (size_t)b * a.nregions;
+    c.theta = a.theta + (size_t)b * a.nregions;
+    c.model = a.group_model;
+    c.h = (double)((const RegionP<T>*)a.regions)[(size_t)b * a.nregions].h;
+    const T* tau = (const T*)a.times + fd.node_off;
+    T* pts = (T*)a.pts + (size_t)ray * a.max_pts * 2;
+
+    const T xt = T(fd.si), yt = T(fd.sj);
+    T bx = T(a.rec_ij[((size_t)b * a.nrec + r) * 2]), by = T(a.rec_ij[((size_t)b * a.nrec + r) * 2 + 1]);
+    T dx = xt - bx, dy = yt - by;
+    int np = 0;
+    pts[0] = bx;
+    pts[1] = by;
+    np = 1;
+    int status = 1;
+    // plane families: normal and node step along the plane
+    const int NX[4] = {1, 0, 1, 1}, NY[4] = {0, 1, -1, 1};
+    const int TXs[4] = {0, 1, 1, 1}, TYs[4] = {1, 0, 1, -1};
+    T cost[33];
+    int pidx[33];
+    while (np < a.max_pts) {
+        const T rx = xt - bx, ry = yt - by;
+        if (sqrt_(rx * rx + ry * ry) < T(a.stop_radius)) {
+            pts[2 * np] = xt;
+            pts[2 * np + 1] = yt;
+            np++;
+            status = 0;
+            break;
+        }
+        const T dl = sqrt_(dx * dx + dy * dy);
+        int fam = 0;
+        T bestc = T(-1);
+        for (int k = 0; k < 4; ++k) {
+            const T nl = sqrt_(T(NX[k] * NX[k] + NY[k] * NY[k]));
+            const T cs = abs_(dx * T(NX[k]) + dy * T(NY[k])) / (dl * nl);
+            if (cs > bestc + T(1e-12)) {
+                bestc = cs;
+                fam = k;
+            }
+        }
+        const T nxf = T(NX[fam]), nyf = T(NY[fam]);
+        const T qB = nxf * bx + nyf * by, qT = nxf * xt + nyf * yt;
+        const T dn = dx * nxf + dy * nyf;
+        const T sg = dn >= T(0) ? T(1) : T(-1);
+        const T scale = sqrt_(nxf * nxf + nyf * nyf);
+        T qn = floor(qB + sg * T(a.plane_step) * scale + T(0.5));
+        if (sg * (qn - qT) > T(0)) qn = floor(qT + T(0.5));
+        if (sg * (qn - qB) < T(0.5)) {
+            pts[2 * np] = xt;
+            pts[2 * np + 1] = yt;
+            np++;
+            status = 0;
+            break;
+        }
+        const T tt = (qn - qB) / dn;
+        const T px = bx + tt * dx, py = by + tt * dy;
+        T bxn, byn;
+        if (fam == 0) {
+            bxn = qn;
+            byn = T(0);
+        } else if (fam == 1) {
+            bxn = T(0);
+            byn = qn;
+        } else if (fam == 2) {
+            bxn = T(0);
+            byn = -qn;
+        } else {
+            bxn = T(0);
+            byn = qn;
+        }
+        const T stx = T(TXs[fam]), sty = T(TYs[fam]);
+        const T pc = fam == 0 ? py : px;
+        const int p0 = (int)floor((double)pc + 0.5);
+        int nc = 0;
+        for (int p = p0 - a.halfwidth; p <= p0 + a.halfwidth; ++p) {
+            const T cx = bxn + T(p) * stx, cy = byn + T(p) * sty;
+            const int ci = (int)cx, cj = (int)cy;
+            if (cx < T(0) || cy < T(0) || ci >= fd.nx || cj >= fd.ny) continue;
+            const T tc = tau[(long long)cj * fd.nx + ci];
+            if (!(tc < alf_inf<T>())) continue;
+            const T sx = cx - bx, sy = cy - by;
+            const T len = sqrt_(sx * sx + sy * sy);
+            T seg = T(0);
+            if (len > T(0)) {
+                const int mn = node_at(c, T(0.5) * (bx + cx), T(0.5) * (by + cy));
+                seg = piece_time(c, mn, len, atan2((double)sy, (double)sx));
+            }
+            cost[nc] = seg + tc;
+            pidx[nc] = p;
+            nc++;
+        }
+        if (nc == 0) break;
+        T best = alf_inf<T>();
+        T bpos = T(0);
+        for (int k = 0; k < nc; ++k) {
+            const bool cl_ok = k > 0 && pidx[k - 1] == pidx[k] - 1;
+            const bool cr_ok = k + 1 < nc && pidx[k + 1] == pidx[k] + 1;
+            const T cl = cl_ok ? cost[k - 1] : alf_inf<T>();
+            const T cr = cr_ok ? cost[k + 1] : alf_inf<T>();
+            if (!(cost[k] < cl && cost[k] <= cr)) continue;
+            T val = cost[k], off = T(0);
+            if (cl_ok && cr_ok) {
+                const T den = cl - T(2) * cost[k] + cr;
+                if (den > T(0)) {
+                    off = (cl - cr) / (T(2) * den);
+                    val = cost[k] - (cl - cr) * (cl - cr) / (T(8) * den);
+                }
+            }
+            if (val < best) {
+                best = val;
+                bpos = T(pidx[k]) + off;
+            }
+        }
+        const T nxp = bxn + bpos * stx, nyp = byn + bpos * sty;
+        dx = nxp - bx;
+        dy = nyp - by;
+        bx = nxp;
+        by = nyp;
+        pts[2 * np] = bx;
+        pts[2 * np + 1] = by;
+        np++;
+    }
+    a.npts[ray] = np;
+    if (a.ray_status) a.ray_status[ray] = status;
+    if (status != 0) atomicCAS(a.error, 0u, (unsigned)ALF_ERR_RAY_INCOMPLETE);
+    if (a.ray_time) {
+        T total = T(0);
+        for (int s = 0; s + 1 < np; ++s) {
+            const T x0 = pts[2 * s], y0 = pts[2 * s + 1], x1 = pts[2 * s + 2], y1 = pts[2 * s + 3];
+            const T ddx = x1 - x0, ddy = y1 - y0;
+            const T len = sqrt_(ddx * ddx + ddy * ddy);
+            if (len == T(0)) continue;
+            const double dir = atan2((double)ddy, (double)ddx);
+            // crossings of x = k + 1/2 and y = k + 1/2 strictly inside the segment, merged in order
+            const bool xinc = ddx > T(0), yinc = ddy > T(0);
+            T kx = xinc ? floor(x0 - T(0.5)) + T(1.5) : ceil(x0 - T(0.5)) - T(0.5);
+            T ky = yinc ? floor(y0 - T(0.5)) + T(1.5) : ceil(y0 - T(0.5)) - T(0.5);
+            T tprev = T(0);
+            for (int guard = 0; guard < 1 << 20; ++guard) {
+                T tx = T(2), ty = T(2);
+                if (ddx != T(0) && (xinc ? kx < x1 : kx > x1)) tx = (kx - x0) / ddx;
+                if (ddy != T(0) && (yinc ? ky < y1 : ky > y1)) ty = (ky - y0) / ddy;
+                T tn = fmin(tx, ty);
+                const bool last = !(tn < T(1));
+                if (last) tn = T(1);
+                if (tn > tprev) {
+                    const T tm = T(0.5) * (tprev + tn);
+                    const int n = node_at(c, x0 + tm * ddx, y0 + tm * ddy);
+                    total += piece_time(c, n, (tn - tprev) * len, dir);
+                    tprev = tn;
+                }
+                if (last) break;
+                if (tx <= ty) kx += xinc ? T(1) : T(-1);
+                if (ty <= tx) ky += yinc ? T(1) : T(-1);
+            }
+        }
+        ((T*)a.ray_time)[ray] = total;
+    }
+}
+
+cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st)
+{
+    const long long nrays = (long long)a.nfields * a.nrec;
+    if (nrays == 0) return cudaSuccess;
+    const int bs = 64;
+    const long long gs = (nrays + bs - 1) / bs;
+    if (precision == ALF_FP64) ray_kernel<double><<<(unsigned)gs, bs, 0, st>>>(a);
+    else ray_kernel<float><<<(unsigned)gs, bs, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace alf

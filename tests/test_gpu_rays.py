@@ -1,0 +1,70 @@
+"""GPU ray tracer against the oracle's, and against the velocity-gradient arc of Sec. 5.2."""
+import numpy as np
+import pytest
+
+from paper_2302_10988_gb300 import workloads as W
+from tests.gpu_helpers import oracle_field, oracle_medium
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2302_10988_gb300 import build
+    build.build()
+    from paper_2302_10988_gb300 import api as A
+    return A
+
+
+def test_rays_fp64_match_oracle(api, oracle):
+    wl = W.homogeneous_ti()
+    P = api.Plan(wl, precision="fp64")
+    th = P.theta_tensor()
+    times, rt = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    assert P.status() == 0
+    tau, orec, fr, M = oracle_field(oracle, wl, 0, 0)
+    src = wl.samples[0].src[0]
+    for r, rec in enumerate(wl.samples[0].rec):
+        opts, ost = oracle.trace_ray(M, tau, rec, src, plane_step=4, halfwidth=8, stop_radius=1.6)
+        n = int(npts[0, 0, r])
+        assert ost == 0 and int(st[0, 0, r]) == 0
+        assert n == len(opts)
+        g = pts[0, 0, r, :n].cpu().numpy()
+        assert np.abs(g - opts).max() < 1e-7
+        assert float(rtime[0, 0, r]) == pytest.approx(oracle.path_time(M, opts), rel=1e-10)
+
+
+def test_rays_fp32_weld(api, oracle):
+    wl = W.weld_single(n=128, h=0.5e-3, rg=8, seed=5, nsrc=2, nrec=8)
+    P = api.Plan(wl, precision="fp32")
+    th = P.theta_tensor()
+    times, rt = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    assert P.status() == 0
+    M = oracle_medium(oracle, wl, 0)
+    for s in range(2):
+        tau, orec, fr, M = oracle_field(oracle, wl, 0, s)
+        for r, rec in enumerate(wl.samples[0].rec):
+            opts, ost = oracle.trace_ray(M, tau, rec, wl.samples[0].src[s])
+            t_o = oracle.path_time(M, opts)
+            assert float(rtime[0, s, r]) == pytest.approx(t_o, rel=2e-3)
+            # the ray time bounds the field's receiver time from above up to the field's error
+            assert float(rtime[0, s, r]) > 0.97 * float(rt[0, s, r])
+
+
+def test_velocity_gradient_ray_gpu(api):
+    wl = W.velocity_gradient()
+    P = api.Plan(wl, precision="fp64", init_radius=1)
+    th = P.theta_tensor()
+    times, rt = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    assert P.status() == 0
+    n = int(npts[0, 0, 0])
+    p = pts[0, 0, 0, :n].cpu().numpy()
+    g, v0 = 21.0, 3021.0
+    cot = ((g * 150) ** 2 + (g * 198 + v0) ** 2 - v0 ** 2) / (2 * g * 150 * v0)
+    cx, cy, R = 1 - v0 / g, 30 + v0 * cot / g, v0 * np.sqrt(1 + cot * cot) / g
+    assert np.abs(np.hypot(p[:, 0] - cx, p[:, 1] - cy) - R).max() < 1.0
+    assert float(rtime[0, 0, 0]) == pytest.approx(5.0884053e-05, rel=5e-4)
