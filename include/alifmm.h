@@ -102,8 +102,8 @@ typedef struct {
     double stop_radius;     /* stop when this close to the target, cells (default 1.6) */
     int max_ray_points;     /* points per ray including both ends (default 512) */
     int max_rounds;         /* livelock guard: sweep rounds per field <= max_rounds * (nx + ny) (default 64) */
-    int cta_threads;        /* threads per sweep CTA (one field per warp): 128, 256 or 512; 0 = autotune */
-    int ctas_per_sm;        /* persistent sweep CTAs per SM, 0 = as many as fit (default 0) */
+    int cta_threads;        /* reserved (0) */
+    int ctas_per_sm;        /* reserved (0) */
     int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
     double band_cells;      /* sweep schedule: nodes later than the front by more than this many
                                cell-crossing times wait for the front (default 4; <= 0: no band) */
@@ -162,9 +162,12 @@ alf_status alf_plan_options(const alf_plan* plan, alf_options* out);
 
 /* Forward solve (Secs. 2, 4): for every field, the near-source initialisation
  * then the ALI local update iterated to its fixed point (the heap FMM's
- * result) by a persistent sweep kernel: each warp takes whole fields and
- * re-evaluates the dirty set of nodes whose neighbourhood changed until it is
- * empty.
+ * result) by bulk-synchronous sweep rounds over all fields of the plan: each
+ * round re-evaluates, in every field, the dirty nodes (those whose
+ * neighbourhood changed) near the front, until every dirty set is empty.
+ * The call enqueues the rounds on `stream` and synchronises it every 32
+ * rounds to read the remaining work, so it returns once the sweep is done
+ * (the finalisation and receiver gather are still enqueued, not waited for).
  *  region_theta   [nsamples][nregions] double, orientation of each region
  *  times          [total nodes] float (ALF_FP32) or double (ALF_FP64), output
  *  rec_times      [nsamples][nsources][nreceivers], same dtype, output; may be NULL

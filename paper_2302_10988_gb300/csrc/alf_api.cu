@@ -151,8 +151,21 @@ const char* alf_last_error(const alf_ctx* ctx) { return ctx ? ctx->err.c_str() :
 static void plan_free(alf_plan* p)
 {
     dfree(p->d_fields);
-    dfree(p->d_ws);
-    dfree(p->d_order);
+    dfree(p->d_list0);
+    dfree(p->d_list1);
+    dfree(p->d_elist);
+    dfree(p->d_efield);
+    dfree(p->d_oldv);
+    dfree(p->d_newv);
+    dfree(p->d_bitmap);
+    dfree(p->d_bm_off);
+    dfree(p->d_cnt);
+    dfree(p->d_ecnt);
+    dfree(p->d_eoff);
+    dfree(p->d_rounds);
+    dfree(p->d_flim);
+    dfree(p->d_pending);
+    if (p->h_pending) cudaFreeHost(p->h_pending);
     dfree(p->d_map);
     dfree(p->d_region_mat);
     dfree(p->d_mats);
@@ -199,7 +212,6 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     }
     if (opt.cta_threads != 0 && opt.cta_threads != 128 && opt.cta_threads != 256 && opt.cta_threads != 512)
         return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 128, 256 or 512");
-    if (opt.cta_threads == 0) opt.cta_threads = 256;
     if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 64) return fail(ctx, ALF_ERR_INVALID_ARG, "ctas_per_sm out of range");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
@@ -301,24 +313,18 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         }
     p->field_off.push_back(node_off);
     p->total_nodes = node_off;
-    const int occ = fim_max_ctas_per_sm(opt.precision, opt.cta_threads);
-    const int per_sm = opt.ctas_per_sm > 0 ? std::min(opt.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    // small batches: narrower CTAs so that the fields spread over all SMs
-    if (opt.cta_threads > 128 && p->nfields < ctx->nsm * per_sm * (opt.cta_threads / 32)) {
-        opt.cta_threads = 128;
+    if (opt.cta_threads == 0) opt.cta_threads = 128;
+    // launch shapes of the sweep: one warp per field for the per-field steps, a
+    // persistent-sized grid for the flat evaluation and marking steps
+    p->grid_fields = std::max(1, std::min((p->nfields + 7) / 8, ctx->nsm * 16));
+    p->grid_eval = ctx->nsm * 16;
+    std::vector<size_t> bm_off(p->nfields);
+    size_t bm_words = 0;
+    for (int f = 0; f < p->nfields; ++f) {
+        bm_off[f] = bm_words;
+        bm_words += ((size_t)p->fields[f].nx * p->fields[f].ny + 31) / 32;
     }
-    const int occ2 = fim_max_ctas_per_sm(opt.precision, opt.cta_threads);
-    const int per_sm2 = opt.ctas_per_sm > 0 ? std::min(opt.ctas_per_sm, std::max(occ2, 1)) : std::max(occ2, 1);
-    const int wpc = opt.cta_threads / 32;
-    p->grid_ctas = std::max(1, std::min(ctx->nsm * per_sm2, (p->nfields + wpc - 1) / wpc));
-    p->sweep_warps = p->grid_ctas * wpc;
-    // per warp: two dirty lists and an evaluation list of max_field_nodes entries, and a bitmap
-    p->ws_stride = 3 * p->max_field_nodes + (p->max_field_nodes + 31) / 32 + 32;
-    std::vector<unsigned> order(p->nfields);
-    for (int f = 0; f < p->nfields; ++f) order[f] = (unsigned)f;
-    std::stable_sort(order.begin(), order.end(), [&](unsigned x, unsigned y) {
-        return (long long)p->fields[x].nx * p->fields[x].ny > (long long)p->fields[y].nx * p->fields[y].ny;
-    });
+    p->bm_words = bm_words;
     p->opt = opt;
 
     cudaSetDevice(ctx->device);
@@ -333,8 +339,29 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         }                                                               \
     } while (0)
     ALLOC(p->d_fields, p->fields.size());
-    ALLOC(p->d_ws, p->ws_stride * (size_t)p->sweep_warps);
-    ALLOC(p->d_order, (size_t)p->nfields);
+    ALLOC(p->d_list0, p->total_nodes);
+    ALLOC(p->d_list1, p->total_nodes);
+    ALLOC(p->d_elist, p->total_nodes);
+    ALLOC(p->d_efield, p->total_nodes);
+    {
+        char* o = nullptr;
+        char* n = nullptr;
+        const size_t tb = opt.precision == ALF_FP64 ? 8 : 4;
+        ALLOC(o, p->total_nodes * tb);
+        p->d_oldv = o;
+        ALLOC(n, p->total_nodes * tb);
+        p->d_newv = n;
+        char* l = nullptr;
+        ALLOC(l, (size_t)p->nfields * tb);
+        p->d_flim = l;
+    }
+    ALLOC(p->d_bitmap, p->bm_words);
+    ALLOC(p->d_bm_off, (size_t)p->nfields);
+    ALLOC(p->d_cnt, 2 * (size_t)p->nfields);
+    ALLOC(p->d_ecnt, (size_t)p->nfields);
+    ALLOC(p->d_eoff, (size_t)p->nfields + 1);
+    ALLOC(p->d_rounds, (size_t)p->nfields);
+    ALLOC(p->d_pending, 1);
     ALLOC(p->d_map, p->total_map);
     ALLOC(p->d_region_mat, (size_t)p->R);
     ALLOC(p->d_mats, (size_t)p->nmat);
@@ -352,7 +379,8 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         p->d_regions64 = r2;
     }
 #undef ALLOC
-    if (cudaMallocHost((void**)&p->h_q, sizeof(QueueState)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&p->h_q, sizeof(QueueState)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->h_pending, sizeof(unsigned long long)) != cudaSuccess) {
         plan_free(p);
         delete p;
         return fail(ctx, ALF_ERR_OOM, "pinned status word");
@@ -363,7 +391,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = up(p->d_fields, p->fields.data(), p->fields.size() * sizeof(FieldDesc));
     if (e == cudaSuccess) e = up(p->d_map, g->region_map, p->total_map * sizeof(uint16_t));
-    if (e == cudaSuccess) e = up(p->d_order, order.data(), order.size() * sizeof(unsigned));
+    if (e == cudaSuccess) e = up(p->d_bm_off, bm_off.data(), bm_off.size() * sizeof(size_t));
     if (e == cudaSuccess) e = up(p->d_region_mat, g->region_material, (size_t)p->R * sizeof(uint16_t));
     if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
     if (e == cudaSuccess) e = up(p->d_h, g->h, (size_t)p->B * sizeof(double));
@@ -423,20 +451,45 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     FimLaunch a;
     a.times = times;
     a.fields = p->d_fields;
-    a.order = p->d_order;
     a.nfields = p->nfields;
     a.region_map = p->d_map;
     a.regions = p->d_regions;
     a.nregions = p->R;
     a.box = p->box;
-    a.ws = p->d_ws;
-    a.ws_stride = p->ws_stride;
-    a.list_cap = (unsigned)p->max_field_nodes;
+    a.list[0] = p->d_list0;
+    a.list[1] = p->d_list1;
+    a.elist = p->d_elist;
+    a.bitmap = p->d_bitmap;
+    a.bm_off = p->d_bm_off;
+    a.cnt = p->d_cnt;
+    a.ecnt = p->d_ecnt;
+    a.eoff = p->d_eoff;
+    a.efield = p->d_efield;
+    a.oldv = p->d_oldv;
+    a.newv = p->d_newv;
+    a.rounds = p->d_rounds;
+    a.flim = p->d_flim;
     a.max_rounds_per_node = (unsigned)p->opt.max_rounds;
     a.band_cells = p->opt.band_cells;
     a.q = p->d_q;
     a.records = records;
-    ALF_CUDA(ctx, launch_fim(prec, p->opt.cta_threads, p->grid_ctas, a, st));
+    ALF_CUDA(ctx, launch_fim_init(prec, a, p->grid_fields, st));
+    // rounds until every dirty set is empty; the work left is read back every
+    // rounds_per_check rounds (rounds of finished fields exit immediately)
+    long long max_total = 0;
+    for (const FieldDesc& fd : p->fields) max_total = std::max(max_total, (long long)(fd.nx + fd.ny));
+    max_total *= p->opt.max_rounds;
+    int parity = 0;
+    for (long long r = 0; r < max_total;) {
+        for (int k = 0; k < p->rounds_per_check; ++k, ++r) {
+            ALF_CUDA(ctx, launch_fim_round(prec, a, parity, p->grid_fields, p->grid_eval, st));
+            parity ^= 1;
+        }
+        ALF_CUDA(ctx, launch_fim_pending(a, parity, p->d_pending, st));
+        ALF_CUDA(ctx, cudaMemcpyAsync(p->h_pending, p->d_pending, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        ALF_CUDA(ctx, cudaStreamSynchronize(st));
+        if (*p->h_pending == 0ull) break;
+    }
     ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times, st));
     return ALF_OK;
 }
@@ -543,7 +596,7 @@ alf_status alf_plan_stats(alf_plan* p, void* stream, uint64_t out[4])
     out[0] = q.visits;
     out[1] = q.rounds;
     out[2] = (uint64_t)p->total_nodes;
-    out[3] = (uint64_t)p->grid_ctas;
+    out[3] = (uint64_t)p->grid_eval;
     return ALF_OK;
 }
 

@@ -113,15 +113,20 @@ ALF_D T phase_L(const RegionP<T>& R, T ux, T uy)
     return T(0.5) * ((al + ga) + sqrt_(dm * dm + T(4) * be * be));
 }
 
+ALF_D float div_(float a, float b) { return __fdividef(a, b); }
+ALF_D double div_(double a, double b) { return a / b; }
+ALF_D float rsqrt_(float v) { return rsqrtf(v); }
+ALF_D double rsqrt_(double v) { return 1.0 / sqrt(v); }
+
 template <typename T>
 ALF_D T stencil_time(int xA, int yA, int xB, int yB, int xC, int yC, T tA, T tB, T tC, const RegionP<T>& R)
 {
-    const T a = (tB - tA) / (tC - tA);
+    const T a = div_(tB - tA, tC - tA);
     const T Ex = T(xA) + a * T(xC - xA);
     const T Ey = T(yA) + a * T(yC - yA);
     const T ux = T(xB) - Ex, uy = T(yB) - Ey;
     const T cross = abs_(T(yB) * Ex - T(xB) * Ey);
-    return tB + R.h * cross / sqrt_(phase_L(R, ux, uy));
+    return tB + R.h * cross * rsqrt_(phase_L(R, ux, uy));
 }
 
 // ---------------------------------------------------------------------------
@@ -174,7 +179,22 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         if (neg_bit(nb[k])) fz |= 1u << k;
         else if (nb[k] < inf) cd |= 1u << k;
     }
-    // pair metrics (+inf when not usable) and times
+    // rank of each candidate in key order (tau, then linear index = static slot order);
+    // frozen slots are known from the start (rank -1), unknown ones never (rank 64)
+    int rk[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? 0 : (((fz >> k) & 1u) ? -1 : 64);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+        for (int m = k + 1; m < 12; ++m) {
+            if (((cd >> k) & (cd >> m) & 1u) == 0u) continue;
+            const bool lt = t[k] < t[m] || (t[k] == t[m] && sord(k) < sord(m));
+            rk[m] += lt ? 1 : 0;
+            rk[k] += lt ? 0 : 1;
+        }
+    const int nc = __popc(cd);
+    // pairs: metric (+inf when not usable) and time
     T pm[16], pv[16];
     unsigned prow_m2 = 0u;  // bit p: member 2 (tau_P > tau_Q)
 #pragma unroll
@@ -187,8 +207,7 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         if (!m1) prow_m2 |= 1u << p;
         pm[p] = inf;
         pv[p] = inf;
-        const bool have = (((fz | cd) >> A) & ((fz | cd) >> P) & ((fz | cd) >> Q) & 1u) != 0u;
-        if (have && tA < tP && tA < tQ) {
+        if (max(rk[A], max(rk[P], rk[Q])) < 64 && tA < tP && tA < tQ) {
             const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
             const int xB = m1 ? sdi(P) : sdi(Q), yB = m1 ? sdj(P) : sdj(Q);
             const int xC = m1 ? sdi(Q) : sdi(P), yC = m1 ? sdj(Q) : sdj(P);
@@ -199,72 +218,61 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
             }
         }
     }
-    // straight-ray fallback through each slot
-    T g[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] = t[k] + ((k >= 8) ? T(2) * R.fb[scls(k)] : R.fb[scls(k)]);
-
-    // walk the thresholds: known(k) = frozen, or candidate with key <= (th_t, th_o)
-    T th_t = -inf;
-    int th_o = -1;
+    // walk the prefixes: at step k the known set is the frozen slots and the candidates of rank <= k
     T u = inf;
     int urec = 255;
     bool done = false;
 #pragma unroll 1
-    for (int it = 0; it < 13; ++it) {
+    for (int k = -1; k < 12; ++k) {
         if (!done) {
-            unsigned known = fz;
+            unsigned known = 0u;
 #pragma unroll
-            for (int k = 0; k < 12; ++k)
-                if (((cd >> k) & 1u) && (t[k] < th_t || (t[k] == th_t && sord(k) <= th_o))) known |= 1u << k;
-            // U(known)
+            for (int q = 0; q < 12; ++q) known |= (rk[q] <= k ? 1u : 0u) << q;
             T bm = inf, bv = inf;
             int br = 255;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const unsigned need = (1u << pa(p)) | (1u << pp(p)) | (1u << pq(p));
-                if ((known & need) == need && pm[p] < bm) {
+            for (int p = 0; p < 8; ++p)
+                if (((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && pm[p] < bm) {
                     bm = pm[p];
                     bv = pv[p];
                     br = 2 * p + ((prow_m2 >> p) & 1u);
                 }
-            }
             if (br == 255) {
 #pragma unroll
-                for (int p = 8; p < 16; ++p) {
-                    const unsigned need = (1u << pa(p)) | (1u << pp(p)) | (1u << pq(p));
-                    if ((known & need) == need && pm[p] < bm) {
+                for (int p = 8; p < 16; ++p)
+                    if (((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && pm[p] < bm) {
                         bm = pm[p];
                         bv = pv[p];
                         br = 2 * p + ((prow_m2 >> p) & 1u);
                     }
-                }
             }
             if (br == 255) {
 #pragma unroll
-                for (int k = 0; k < 12; ++k)
-                    if (((known >> k) & 1u) && g[k] < bv) {
-                        bv = g[k];
-                        br = 32 + k;
+                for (int q = 0; q < 12; ++q) {
+                    if (!((known >> q) & 1u)) continue;
+                    const T gq = t[q] + ((q >= 8) ? T(2) * R.fb[scls(q)] : R.fb[scls(q)]);
+                    if (gq < bv) {
+                        bv = gq;
+                        br = 32 + q;
                     }
+                }
             }
             u = bv;
             urec = br;
-            // next threshold: the smallest candidate key above the current one
-            T nt = inf;
-            int no = 99;
+            if (k + 1 >= nc) {
+                done = true;
+            } else {
+                // the neighbour of rank k + 1; stop when D's key (u, me) precedes it
+                T nt = inf;
+                int no = 0;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                if (!((cd >> k) & 1u) || ((known >> k) & 1u)) continue;
-                if (t[k] < nt || (t[k] == nt && sord(k) < no)) {
-                    nt = t[k];
-                    no = sord(k);
-                }
+                for (int q = 0; q < 12; ++q)
+                    if (rk[q] == k + 1) {
+                        nt = t[q];
+                        no = sord(q);
+                    }
+                if (u < nt || (u == nt && 12 < no)) done = true;
             }
-            // stop when nothing is left or D's key precedes the next neighbour's
-            if (no == 99 || u < nt || (u == nt && 12 < no)) done = true;
-            th_t = nt;
-            th_o = no;
         }
         if (__all_sync(__activemask(), done)) break;
     }

@@ -36,15 +36,23 @@ struct QueueState {
 struct FimLaunch {
     void* times;
     const FieldDesc* fields;
-    const unsigned* order;         // field processing order (largest first)
     int nfields;
     const uint16_t* region_map;
     const void* regions;  // RegionP<T>[nsamples][nregions]
     int nregions;
     int box;                       // half-width of the frozen box around each source
-    unsigned* ws;                  // per-warp workspace: two lists of list_cap entries + bitmap
-    size_t ws_stride;              // words per warp
-    unsigned list_cap;
+    unsigned* list[2];             // dirty lists, segments at the fields' node offsets
+    unsigned* elist;               // evaluation lists, same segments
+    unsigned* bitmap;              // dirty bitmaps, field f at word bm_off[f]
+    const size_t* bm_off;
+    unsigned* cnt;                 // [2][nfields] dirty-list sizes (by round parity)
+    unsigned* ecnt;                // [nfields] evaluation-list sizes
+    unsigned* eoff;                // [nfields + 1] exclusive scan of ecnt
+    unsigned* efield;              // [total nodes] field of each evaluation slot
+    void* oldv;                    // [total nodes] time before / after each evaluation
+    void* newv;
+    unsigned* rounds;              // [nfields] rounds taken
+    void* flim;                    // [nfields] T + band of the current round
     unsigned max_rounds_per_node;  // round cap = this x (nx + ny)
     double band_cells;             // evaluation band beyond the front, in cells of cell_time (<= 0: none)
     QueueState* q;
@@ -60,8 +68,10 @@ cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fiel
                                const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
                                const double* theta, const double* h, int nregions, int r0, int group_model,
                                unsigned* frozen_bits, int box, cudaStream_t st);
-cudaError_t launch_fim(int precision, int threads, int grid, const FimLaunch& a, cudaStream_t st);
-int fim_max_ctas_per_sm(int precision, int threads);
+cudaError_t launch_fim_init(int precision, const FimLaunch& a, int grid_fields, cudaStream_t st);
+cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int grid_fields, int grid_eval,
+                             cudaStream_t st);
+cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, cudaStream_t st);
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
@@ -113,7 +123,9 @@ struct alf_plan {
     size_t total_nodes = 0;
     size_t total_map = 0;
     size_t max_field_nodes = 0;
-    int grid_ctas = 0;
+    int grid_fields = 0;  // CTAs of the per-field sweep steps (one warp per field)
+    int grid_eval = 0;    // CTAs of the flat evaluation and marking steps
+    size_t bm_words = 0;
     int box = 0;  // half-width of the frozen box around each source
     // device
     alf::FieldDesc* d_fields = nullptr;
@@ -124,10 +136,23 @@ struct alf_plan {
     int32_t* d_rec = nullptr;
     void* d_regions = nullptr;    // RegionP<T> of the plan precision
     void* d_regions64 = nullptr;  // RegionP<double> for the FP64 check
-    unsigned* d_ws = nullptr;     // per-warp dirty lists and bitmaps
-    unsigned* d_order = nullptr;  // field order of the sweep
-    int sweep_warps = 0;
-    size_t ws_stride = 0;
+    // sweep workspace
+    unsigned* d_list0 = nullptr;
+    unsigned* d_list1 = nullptr;
+    unsigned* d_elist = nullptr;
+    unsigned* d_efield = nullptr;
+    void* d_oldv = nullptr;
+    void* d_newv = nullptr;
+    unsigned* d_bitmap = nullptr;
+    size_t* d_bm_off = nullptr;
+    unsigned* d_cnt = nullptr;
+    unsigned* d_ecnt = nullptr;
+    unsigned* d_eoff = nullptr;
+    unsigned* d_rounds = nullptr;
+    void* d_flim = nullptr;
+    unsigned long long* d_pending = nullptr;
+    unsigned long long* h_pending = nullptr;  // pinned
+    int rounds_per_check = 32;
     alf::QueueState* d_q = nullptr;
     unsigned* d_ray_error = nullptr;
     unsigned* d_frozen = nullptr;  // per-field bitmap of frozen nodes in the source box

@@ -4,8 +4,8 @@
 //                 step times of the fallback (FP64 group->phase inversion)
 //  fill_inf       every node of every field := +inf
 //  init_radius    frozen straight-ray times around each source (Sec. 4.4)
-//  fim            persistent warp-per-field dirty-set sweep of the local operator F
-//                 to its fixed point (fields taken from a global counter)
+//  fim_*          bulk-synchronous dirty-set sweep of the local operator F to its
+//                 fixed point, all fields of the batch in every round
 //  finalize       clears the frozen marks and gathers receiver times
 //  check64        FP64 evaluation of F at every node of a solved field
 #include <cstdio>
@@ -156,39 +156,33 @@ cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fiel
 }
 
 // ---------------------------------------------------------------------------
-// fim: persistent warp-per-field dirty-set sweep
+// fim: bulk-synchronous dirty-set sweep over all fields at once
 // ---------------------------------------------------------------------------
-// Each warp takes whole fields from a global counter (largest fields first).
-// For one field it keeps the dirty set -- nodes that may not be at the fixed
-// point of F -- as a list in its own workspace, with a bitmap so that a node
-// is listed at most once.  A round
-//   1. takes T = the smallest time in the dirty set (warp min-reduction);
-//   2. evaluates F at every dirty node that is still unknown (+inf) or not
-//      later than T + band; later nodes wait for the front, so that they are
-//      not re-evaluated for every transient change of their upwind neighbours
-//      (the band keeps the sweep close to the heap's order while a whole band
-//      of the front is in flight);
-//   3. writes the changed times, and marks dirty every non-frozen diamond
-//      neighbour m of a changed node n whose time can depend on n: m unknown,
-//      or m not earlier than n's old or new time (F at m only reads the
-//      neighbours that precede m in key order).
-// The nodes due in a round are first compacted into an evaluation list, which
-// is worked in chunks of 32 x kPerLane entries: a chunk is evaluated from the
-// times as they stand (Jacobi within the chunk), then written, then its dirty
-// marks are set, with __syncwarp between the three steps, so the marking rule
-// always compares against written times.  The field is at the
-// fixed point of F when the dirty set is empty.  Frozen nodes carry the sign
-// bit and are never listed.
-ALF_D unsigned ws_push(unsigned* bitmap, unsigned* list, unsigned* cnt, unsigned node)
-{
-    const unsigned bit = 1u << (node & 31u);
-    if (!(atomicOr(bitmap + (node >> 5), bit) & bit)) {
-        list[atomicAdd(cnt, 1u)] = node;
-        return 1u;
-    }
-    return 0u;
-}
-
+// Every field keeps its dirty set -- nodes that may not be at the fixed point
+// of F -- as a list (segment of the packed lists at the field's node offset)
+// and a bitmap, so that a node is listed at most once.  A round is four
+// launches over all fields:
+//   prep   one warp per field: T = the smallest time in the dirty set; the
+//          nodes that are unknown (+inf) or not later than T + band move to
+//          the field's evaluation list (bitmap bit cleared); later nodes stay
+//          dirty for the next round (they wait for the front, so that they
+//          are not re-evaluated for every transient change upwind -- the band
+//          keeps the sweep close to the heap's order with a whole band of the
+//          front in flight);
+//   scan   exclusive scan of the evaluation-list sizes (one flat index space);
+//   eval   one thread per listed node of every field: F, time written in
+//          place, old and new time kept for the marking step;
+//   mark   for every changed node n, every known non-frozen diamond
+//          neighbour m whose time can depend on n -- m not earlier than n's
+//          old or new time (F at m only reads the neighbours that precede m in
+//          key order) -- is marked dirty for the next round; unknown
+//          neighbours are marked (for their first evaluation) only by a node
+//          whose time is inside the band, and a node outside the band with
+//          unknown neighbours marks itself, to seed them once the front
+//          arrives.  This keeps the dirty sets a thin shell around the front.
+// The marking runs after all writes of the round, so it compares against
+// written times.  A field is at the fixed point of F when its dirty set is
+// empty.  Frozen nodes carry the sign bit and are never listed.
 ALF_D unsigned order_key(float v) { return __float_as_uint(v); }  // v >= 0
 ALF_D unsigned long long order_key(double v) { return (unsigned long long)__double_as_longlong(v); }
 ALF_D float from_key(unsigned k, float) { return __uint_as_float(k); }
@@ -203,189 +197,269 @@ ALF_D unsigned long long warp_min(unsigned long long v)
     return v;
 }
 
-constexpr int kPerLane = 2;
-
-template <typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) fim_kernel(FimLaunch a)
+// first dirty set of every field: the non-frozen nodes around the frozen box
+template <typename T>
+__global__ void fim_init_kernel(FimLaunch a)
 {
-    __shared__ unsigned s_cnt[WARPS], s_ecnt[WARPS];
-    const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    const size_t gw = (size_t)blockIdx.x * WARPS + wib;
-    unsigned* const ws = a.ws + gw * a.ws_stride;
-    unsigned* const elist = ws + 2 * (size_t)a.list_cap;
-    unsigned* const bitmap = ws + 3 * (size_t)a.list_cap;
-    unsigned* const cnt = s_cnt + wib;
-    unsigned* const ecnt = s_ecnt + wib;
-    T* times = (T*)a.times;
-    const RegionP<T>* regions = (const RegionP<T>*)a.regions;
-
-    for (;;) {
-        unsigned fo = 0;
-        if (lane == 0) fo = atomicAdd(&a.q->head, 1u);
-        fo = __shfl_sync(0xffffffffu, fo, 0);
-        if (fo >= (unsigned)a.nfields || ld_volatile(&a.q->error) != 0u) return;
-        const unsigned f = a.order[fo];
+    const unsigned lane = threadIdx.x & 31u;
+    const size_t nw = (size_t)gridDim.x * blockDim.x / 32;
+    for (size_t f = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < (size_t)a.nfields; f += nw) {
         const FieldDesc fd = a.fields[f];
         const int nx = fd.nx, ny = fd.ny;
-        const unsigned N = (unsigned)(nx * ny);
-        T* tf = times + fd.node_off;
-        const RegionP<T>* reg = regions + (size_t)fd.sample * a.nregions;
-        const uint16_t* map = a.region_map + fd.map_off;
-        const T band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : alf_inf<T>();
-        unsigned* listA = ws;
-        unsigned* listB = ws + a.list_cap;
-
-        for (unsigned w = lane; w < (N + 31u) / 32u; w += 32u) bitmap[w] = 0u;
-        if (lane == 0) *cnt = 0u;
+        const T* tf = (const T*)a.times + fd.node_off;
+        unsigned* bm = a.bitmap + a.bm_off[f];
+        unsigned* list = a.list[0] + fd.node_off;
+        const unsigned words = (unsigned)((nx * ny + 31) / 32);
+        for (unsigned w = lane; w < words; w += 32u) bm[w] = 0u;
         __syncwarp();
-        {   // first dirty set: the non-frozen nodes around the frozen box
-            const int r = a.box + 2, w = 2 * r + 1;
-            for (int k = (int)lane; k < w * w; k += 32) {
+        const int r = a.box + 2, w = 2 * r + 1;
+        unsigned cnt = 0;
+        for (int base = 0; base < w * w; base += 32) {
+            const int k = base + (int)lane;
+            bool take = false;
+            unsigned n = 0;
+            if (k < w * w) {
                 const int i = fd.si + k % w - r, j = fd.sj + k / w - r;
-                if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
-                const unsigned n = (unsigned)(j * nx + i);
-                if (!neg_bit(__ldcg(tf + n))) ws_push(bitmap, listA, cnt, n);
+                if (i >= 0 && j >= 0 && i < nx && j < ny) {
+                    n = (unsigned)(j * nx + i);
+                    take = !neg_bit(__ldcg(tf + n));
+                }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                list[cnt + __popc(bal & ((1u << lane) - 1u))] = n;
+                atomicOr(bm + (n >> 5), 1u << (n & 31u));
+            }
+            cnt += __popc(bal);
         }
-        __syncwarp();
-        unsigned nact = *cnt;
-        unsigned rounds = 0;
-        unsigned long long evals = 0;
-        const unsigned max_rounds = a.max_rounds_per_node * (unsigned)(nx + ny);
-        while (nact > 0) {
-            if (++rounds > max_rounds) {
-                if (lane == 0) set_error(a.q, ALF_ERR_NOT_CONVERGED);
-                break;
-            }
-            // 1. front time
-            auto m = order_key(alf_inf<T>());
-            for (unsigned k = lane; k < nact; k += 32u) {
-                const auto v = order_key(__ldcg(tf + listA[k]));
-                m = v < m ? v : m;
-            }
-            const T lim = from_key(warp_min(m), T(0)) + band;
-            __syncwarp();
-            if (lane == 0) {
-                *cnt = 0u;
-                *ecnt = 0u;
-            }
-            __syncwarp();
-            // 2a. nodes due for evaluation leave the set and go to the evaluation list;
-            //     nodes far ahead of the front stay dirty (their bit stays set)
-            for (unsigned k = lane; k < nact; k += 32u) {
-                const unsigned n = listA[k];
-                const T t = __ldcg(tf + n);
-                if (t <= lim || !(t < alf_inf<T>())) {
-                    atomicAnd(bitmap + (n >> 5), ~(1u << (n & 31u)));
-                    elist[atomicAdd(ecnt, 1u)] = n;
-                } else {
-                    listB[atomicAdd(cnt, 1u)] = n;
-                }
-            }
-            __syncwarp();
-            const unsigned ne = *ecnt;
-            for (unsigned base = 0; base < ne; base += 32u * kPerLane) {
-                unsigned node[kPerLane];
-                T oldv[kPerLane], newv[kPerLane];
-                bool ev[kPerLane];
-                // 2b. evaluate a chunk with the times as they stand
-#pragma unroll
-                for (int r = 0; r < kPerLane; ++r) {
-                    const unsigned k = base + (unsigned)r * 32u + lane;
-                    ev[r] = k < ne;
-                    node[r] = ev[r] ? elist[k] : 0u;
-                }
-#pragma unroll
-                for (int r = 0; r < kPerLane; ++r) {
-                    oldv[r] = newv[r] = alf_inf<T>();
-                    if (!ev[r]) continue;
-                    const unsigned n = node[r];
-                    oldv[r] = __ldcg(tf + n);
-                    const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                    T nb[12];
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) {
-                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
-                        nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? __ldcg(tf + jj * nx + ii) : alf_inf<T>();
-                    }
-                    const RegionP<T> R = reg[__ldg(map + n)];
-                    int rec;
-                    newv[r] = local_F<T>(nb, (int)n, nx, R, rec);
-                    if (a.records) a.records[fd.node_off + n] = (uint8_t)rec;
-                    ++evals;
-                }
-                __syncwarp();
-                // 2c. write the changed times
-#pragma unroll
-                for (int r = 0; r < kPerLane; ++r)
-                    if (ev[r] && !same_bits(newv[r], oldv[r])) __stcg(tf + node[r], newv[r]);
-                __syncwarp();
-                // 3. mark the neighbours that can depend on a changed node
-#pragma unroll
-                for (int r = 0; r < kPerLane; ++r) {
-                    if (!ev[r] || same_bits(newv[r], oldv[r])) continue;
-                    const unsigned n = node[r];
-                    const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                    const T lo = newv[r] < oldv[r] ? newv[r] : oldv[r];
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) {
-                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
-                        if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
-                        const unsigned mm = (unsigned)(jj * nx + ii);
-                        const T tm = __ldcg(tf + mm);
-                        if (neg_bit(tm)) continue;  // frozen
-                        if (!(tm < alf_inf<T>()) || lo <= tm) ws_push(bitmap, listB, cnt, mm);
-                    }
-                }
-                __syncwarp();
-            }
-            nact = *cnt;
-            unsigned* t = listA;
-            listA = listB;
-            listB = t;
-            __syncwarp();
-        }
-        for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
         if (lane == 0) {
-            atomicAdd(&a.q->visits, evals);
-            atomicAdd(&a.q->rounds, (unsigned long long)rounds);
+            a.cnt[f] = cnt;
+            a.cnt[a.nfields + f] = 0u;
+            a.rounds[f] = 0u;
         }
-        __syncwarp();
     }
 }
 
-template <typename T, int WARPS>
-static cudaError_t fim_t(int grid, const FimLaunch& a, cudaStream_t st)
+template <typename T>
+__global__ void fim_prep_kernel(FimLaunch a, int parity)
 {
-    fim_kernel<T, WARPS><<<grid, 32 * WARPS, 0, st>>>(a);
+    const unsigned lane = threadIdx.x & 31u;
+    const size_t nw = (size_t)gridDim.x * blockDim.x / 32;
+    unsigned* cur_cnt = a.cnt + (size_t)parity * a.nfields;
+    unsigned* nxt_cnt = a.cnt + (size_t)(parity ^ 1) * a.nfields;
+    unsigned long long pending = 0;
+    for (size_t f = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < (size_t)a.nfields; f += nw) {
+        const unsigned nact = cur_cnt[f];
+        const FieldDesc fd = a.fields[f];
+        if (nact == 0u || a.rounds[f] >= a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny)) {
+            if (lane == 0) {
+                if (nact != 0u) set_error(a.q, ALF_ERR_NOT_CONVERGED);  // livelock guard: the field is abandoned
+                a.ecnt[f] = 0u;
+                nxt_cnt[f] = 0u;
+            }
+            continue;
+        }
+        const T* tf = (const T*)a.times + fd.node_off;
+        const unsigned* listA = a.list[parity] + fd.node_off;
+        unsigned* listB = a.list[parity ^ 1] + fd.node_off;
+        unsigned* el = a.elist + fd.node_off;
+        unsigned* bm = a.bitmap + a.bm_off[f];
+        auto m = order_key(alf_inf<T>());
+        for (unsigned k = lane; k < nact; k += 32u) {
+            const auto v = order_key(__ldcg(tf + listA[k]));
+            m = v < m ? v : m;
+        }
+        const T band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : alf_inf<T>();
+        const T lim = from_key(warp_min(m), T(0)) + band;
+        unsigned ne = 0, nc = 0;
+        for (unsigned base = 0; base < nact; base += 32u) {
+            const unsigned k = base + lane;
+            bool in = k < nact, ev = false;
+            unsigned n = 0;
+            if (in) {
+                n = listA[k];
+                const T t = __ldcg(tf + n);
+                ev = t <= lim || !(t < alf_inf<T>());
+            }
+            const unsigned be = __ballot_sync(0xffffffffu, in && ev), bc = __ballot_sync(0xffffffffu, in && !ev);
+            const unsigned below = (1u << lane) - 1u;
+            if (in && ev) {
+                el[ne + __popc(be & below)] = n;
+                atomicAnd(bm + (n >> 5), ~(1u << (n & 31u)));
+            } else if (in) {
+                listB[nc + __popc(bc & below)] = n;
+            }
+            ne += __popc(be);
+            nc += __popc(bc);
+        }
+        if (lane == 0) {
+            a.ecnt[f] = ne;
+            nxt_cnt[f] = nc;
+            a.rounds[f] += 1u;
+            ((T*)a.flim)[f] = lim;
+        }
+        pending += nact;
+    }
+    if (lane == 0 && pending) atomicAdd(&a.q->visits, pending);
+}
+
+// exclusive scan of the per-field evaluation counts (one block)
+__global__ void fim_scan_kernel(FimLaunch a)
+{
+    __shared__ unsigned s[1024];
+    const int n = a.nfields;
+    const int per = (n + 1023) / 1024;
+    const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+    unsigned sum = 0;
+    for (int f = b0; f < b1; ++f) sum += a.ecnt[f];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = s[threadIdx.x] - sum;
+    for (int f = b0; f < b1; ++f) {
+        a.eoff[f] = run;
+        run += a.ecnt[f];
+    }
+    if (threadIdx.x == 1023) a.eoff[n] = s[1023];
+}
+
+ALF_D int field_of(const unsigned* eoff, int nfields, unsigned e)
+{
+    int lo = 0, hi = nfields;  // largest f with eoff[f] <= e
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(eoff + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) fim_eval_kernel(FimLaunch a)
+{
+    const unsigned E = a.eoff[a.nfields];
+    T* times = (T*)a.times;
+    T* oldv = (T*)a.oldv;
+    T* newv = (T*)a.newv;
+    const RegionP<T>* regions = (const RegionP<T>*)a.regions;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+        const int f = field_of(a.eoff, a.nfields, e);
+        const FieldDesc fd = a.fields[f];
+        const int nx = fd.nx, ny = fd.ny;
+        T* tf = times + fd.node_off;
+        const unsigned n = a.elist[fd.node_off + (e - a.eoff[f])];
+        const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+        T nb[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+            nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? __ldcg(tf + jj * nx + ii) : alf_inf<T>();
+        }
+        const T old = __ldcg(tf + n);
+        const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + __ldg(a.region_map + fd.map_off + n)];
+        int rec;
+        const T v = local_F<T>(nb, (int)n, nx, R, rec);
+        if (a.records) a.records[fd.node_off + n] = (uint8_t)rec;
+        if (!same_bits(v, old)) __stcg(tf + n, v);
+        oldv[e] = old;
+        newv[e] = v;
+        a.efield[e] = (unsigned)f;
+    }
+}
+
+template <typename T>
+__global__ void fim_mark_kernel(FimLaunch a, int parity)
+{
+    const unsigned E = a.eoff[a.nfields];
+    const T* times = (const T*)a.times;
+    const T* oldv = (const T*)a.oldv;
+    const T* newv = (const T*)a.newv;
+    const T* flim = (const T*)a.flim;
+    unsigned* nxt_cnt = a.cnt + (size_t)(parity ^ 1) * a.nfields;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+        const T o = oldv[e], v = newv[e];
+        const unsigned f = a.efield[e];
+        const bool changed = !same_bits(o, v);
+        const bool inband = v <= flim[f];
+        if (!changed && !inband) continue;
+        const FieldDesc fd = a.fields[f];
+        const int nx = fd.nx, ny = fd.ny;
+        const T* tf = times + fd.node_off;
+        const unsigned n = a.elist[fd.node_off + (e - a.eoff[f])];
+        const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+        const T lo = v < o ? v : o;
+        unsigned* bm = a.bitmap + a.bm_off[f];
+        unsigned* listB = a.list[parity ^ 1] + fd.node_off;
+        auto push = [&](unsigned m) {
+            const unsigned bit = 1u << (m & 31u);
+            if (!(atomicOr(bm + (m >> 5), bit) & bit)) listB[atomicAdd(nxt_cnt + f, 1u)] = m;
+        };
+        bool seeds_later = false;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+            if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+            const unsigned m = (unsigned)(jj * nx + ii);
+            const T tm = __ldcg(tf + m);
+            if (neg_bit(tm)) continue;  // frozen
+            if (tm < alf_inf<T>()) {
+                if (changed && lo <= tm) push(m);
+            } else if (inband) {
+                push(m);             // first evaluation of an unknown neighbour
+            } else {
+                seeds_later = true;  // it is seeded when this node is in the band
+            }
+        }
+        if (seeds_later && v < alf_inf<T>()) push(n);
+    }
+}
+
+// work left after the last round: sum of the next-list sizes
+__global__ void fim_pending_kernel(FimLaunch a, int parity, unsigned long long* out)
+{
+    const unsigned* c = a.cnt + (size_t)parity * a.nfields;
+    unsigned long long s = 0;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < a.nfields; f += gridDim.x * blockDim.x) s += c[f];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+template <typename T>
+static cudaError_t fim_round_t(const FimLaunch& a, int parity, int grid_fields, int grid_eval, cudaStream_t st)
+{
+    fim_prep_kernel<T><<<grid_fields, 256, 0, st>>>(a, parity);
+    fim_scan_kernel<<<1, 1024, 0, st>>>(a);
+    fim_eval_kernel<T><<<grid_eval, 128, 0, st>>>(a);
+    fim_mark_kernel<T><<<grid_eval, 256, 0, st>>>(a, parity);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fim(int precision, int threads, int grid, const FimLaunch& a, cudaStream_t st)
+cudaError_t launch_fim_init(int precision, const FimLaunch& a, int grid_fields, cudaStream_t st)
 {
-    if (precision == ALF_FP64) {
-        if (threads == 128) return fim_t<double, 4>(grid, a, st);
-        if (threads == 512) return fim_t<double, 16>(grid, a, st);
-        return fim_t<double, 8>(grid, a, st);
-    }
-    if (threads == 128) return fim_t<float, 4>(grid, a, st);
-    if (threads == 512) return fim_t<float, 16>(grid, a, st);
-    return fim_t<float, 8>(grid, a, st);
+    if (precision == ALF_FP64) fim_init_kernel<double><<<grid_fields, 256, 0, st>>>(a);
+    else fim_init_kernel<float><<<grid_fields, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
-template <typename T, int WARPS>
-static int occ_fim()
+cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int grid_fields, int grid_eval,
+                             cudaStream_t st)
 {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_kernel<T, WARPS>, 32 * WARPS, 0);
-    return n;
+    return precision == ALF_FP64 ? fim_round_t<double>(a, parity, grid_fields, grid_eval, st)
+                                 : fim_round_t<float>(a, parity, grid_fields, grid_eval, st);
 }
 
-int fim_max_ctas_per_sm(int precision, int threads)
+cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st)
 {
-    if (precision == ALF_FP64)
-        return threads == 128 ? occ_fim<double, 4>() : threads == 512 ? occ_fim<double, 16>() : occ_fim<double, 8>();
-    return threads == 128 ? occ_fim<float, 4>() : threads == 512 ? occ_fim<float, 16>() : occ_fim<float, 8>();
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    fim_pending_kernel<<<64, 256, 0, st>>>(a, parity, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
