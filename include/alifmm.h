@@ -232,6 +232,37 @@ alf_status alf_plan_stats(alf_plan* plan, void* stream, uint64_t out[4]);
 alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, int group_model, int precision,
                              const double* angles, double* out, int n, void* stream);
 
+/* Forward solve of ONE field that allocates no device memory (the paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- an application whose device memory belongs to another
+ * allocator, or a latency-bound loop in which cudaMalloc/cudaFree, which can
+ * synchronise the device, are not allowed).  It runs the same kernels as
+ * alf_solve in FP32 with the radius initialisation, but keeps every workspace
+ * in a fixed device array inside the library (about 7 MB per GPU that loads
+ * the library, held until the process exits).
+ * Limits: nx*ny <= 512*512 nodes, nregions <= 1024, nmaterials <= 64,
+ * init_radius <= 8; larger inputs are rejected with ALF_ERR_INVALID_ARG and a
+ * message in err.
+ *  cuda_device              device to run on (made current)
+ *  materials[nmaterials]    host
+ *  region_material[nregions], region_theta[nregions] (double), region_map[ny][nx]   device, input
+ *  h, (si, sj)              spacing (m) and source node
+ *  group_model              alf_group_model
+ *  times[ny][nx]            device float, output (caller-owned)
+ *  stream                   cudaStream_t as void*; the call synchronises it
+ *  err, err_len             host buffer for a message (may be NULL)
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (other streams or
+ * host threads) race on it.  Returns ALF_OK, ALF_ERR_INVALID_ARG,
+ * ALF_ERR_OUT_OF_GRID, ALF_ERR_NONPHYSICAL_MATERIAL, ALF_ERR_CUDA or
+ * ALF_ERR_NOT_CONVERGED. */
+alf_status alf_solve_field_noalloc(int cuda_device, const alf_material* materials, int nmaterials,
+                                   const uint16_t* region_material, int nregions, const double* region_theta,
+                                   const uint16_t* region_map, int nx, int ny, double h, int si, int sj,
+                                   int init_radius, int group_model, float* times, void* stream, char* err,
+                                   size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
 EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error", "alf_plan_create",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
            "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats",
-           "alf_eval_velocity")
+           "alf_eval_velocity", "alf_solve_field_noalloc")
 
 
 class AlfError(RuntimeError):
@@ -100,6 +100,10 @@ def load(path: str = LIB_PATH):
         L.alf_sync_status.argtypes = [vp, vp, P(C.c_int32)]
         L.alf_plan_stats.restype = C.c_int
         L.alf_plan_stats.argtypes = [vp, vp, P(C.c_uint64)]
+        L.alf_solve_field_noalloc.restype = C.c_int
+        L.alf_solve_field_noalloc.argtypes = [C.c_int, P(alf_material), C.c_int, vp, C.c_int, vp, vp, C.c_int,
+                                              C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
+                                              C.c_char_p, C.c_size_t]
         L.alf_eval_velocity.restype = C.c_int
         L.alf_eval_velocity.argtypes = [vp, P(alf_material), C.c_int, C.c_int, C.c_int, vp, vp, C.c_int, vp]
         _lib = L
@@ -190,3 +194,14 @@ def alf_plan_stats(ctx, plan, stream):
 def alf_eval_velocity(ctx, mat: alf_material, kind, group_model, precision, angles_ptr, out_ptr, n, stream):
     _check(ctx, load().alf_eval_velocity(ctx, C.byref(mat), int(kind), int(group_model), int(precision),
                                          angles_ptr, out_ptr, int(n), stream))
+
+
+def alf_solve_field_noalloc(device, materials, nmaterials, region_material_ptr, nregions, theta_ptr, region_map_ptr,
+                            nx, ny, h, si, sj, init_radius, group_model, times_ptr, stream):
+    """Allocation-free single-field solve; returns (status, message)."""
+    buf = C.create_string_buffer(256)
+    code = load().alf_solve_field_noalloc(int(device), materials, int(nmaterials), region_material_ptr,
+                                          int(nregions), theta_ptr, region_map_ptr, int(nx), int(ny), float(h),
+                                          int(si), int(sj), int(init_radius), int(group_model), times_ptr, stream,
+                                          buf, 256)
+    return int(code), buf.value.decode()
