@@ -981,3 +981,94 @@ int om_init_hierarchy(const om_medium* M, int si, int sj, int nlev, const int* d
     free(pt);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the solve (reverse mode), for the misfit gradient.    */
+/* Every non-frozen node's time is the chosen stencil (or fallback) applied  */
+/* to at most three earlier nodes and to the orientation at the node; a      */
+/* frozen node's time is the straight-ray time from the source, which        */
+/* depends on the orientation at the source.  Walking the nodes in reverse   */
+/* acceptance order, lambda_D = seed_D + sum over later users E of           */
+/* lambda_E d tau_E / d tau_D, and dL/dtheta of a region sums                */
+/* lambda_D d tau_D / d theta_D over its nodes (frozen nodes: the source's   */
+/* region).  The local partial derivatives are central differences of the    */
+/* local formulas above (steps 1e-4 of the stencil's time span, 1e-6 rad).   */
+/* ------------------------------------------------------------------------ */
+static double stencil_time_theta(const om_medium* M, int d, const double xa[3], const double ya[3], double tA,
+                                 double tB, double tC, double theta)
+{
+    double* th = (double*)M->theta; /* the formula reads the orientation of D from the medium */
+    double keep = th[d];
+    th[d] = theta;
+    double v = stencil_time(M, d, xa, ya, tA, tB, tC);
+    th[d] = keep;
+    return v;
+}
+
+/* seeds[node] = dL/dtau at that node; region[node] = region index of the node;
+ * grad[nregions] += dL/dtheta.  order = acceptance ranks from om_fmm. */
+void om_adjoint(const om_medium* M, const uint8_t* frozen, const double* tau, const int16_t* rec,
+                const int32_t* order, const double* seeds, int si, int sj, const int32_t* region, int nregions,
+                double* grad)
+{
+    int nx = M->nx, N = M->nx * M->ny;
+    double* lam = (double*)malloc(sizeof(double) * (size_t)N);
+    int* byrank = (int*)malloc(sizeof(int) * (size_t)N);
+    int nacc = 0;
+    for (int n = 0; n < N; ++n) {
+        lam[n] = seeds[n];
+        if (order[n] >= 0) nacc = order[n] + 1 > nacc ? order[n] + 1 : nacc;
+    }
+    for (int n = 0; n < N; ++n)
+        if (order[n] >= 0) byrank[order[n]] = n;
+    (void)nregions;
+    for (int k = nacc - 1; k >= 0; --k) {
+        int d = byrank[k];
+        int i = d % nx, j = d / nx;
+        int r = rec[d];
+        const double th0 = M->theta[d];
+        if (r >= 0 && r < 32) {
+            const int* s = STENCIL[r];
+            double xa[3] = {s[0], s[2], s[4]}, ya[3] = {s[1], s[3], s[5]};
+            int nA = (j + s[1]) * nx + i + s[0], nB = (j + s[3]) * nx + i + s[2], nC = (j + s[5]) * nx + i + s[4];
+            double tA = tau[nA], tB = tau[nB], tC = tau[nC];
+            double e = 1e-4 * (tC - tA);
+            double dA = (stencil_time(M, d, xa, ya, tA + e, tB, tC) - stencil_time(M, d, xa, ya, tA - e, tB, tC)) / (2 * e);
+            double dB = (stencil_time(M, d, xa, ya, tA, tB + e, tC) - stencil_time(M, d, xa, ya, tA, tB - e, tC)) / (2 * e);
+            double dC = (stencil_time(M, d, xa, ya, tA, tB, tC + e) - stencil_time(M, d, xa, ya, tA, tB, tC - e)) / (2 * e);
+            double dT = (stencil_time_theta(M, d, xa, ya, tA, tB, tC, th0 + 1e-6)
+                         - stencil_time_theta(M, d, xa, ya, tA, tB, tC, th0 - 1e-6)) / 2e-6;
+            lam[nA] += lam[d] * dA;
+            lam[nB] += lam[d] * dB;
+            lam[nC] += lam[d] * dC;
+            grad[region[d]] += lam[d] * dT;
+        } else if (r >= 32) {
+            int k2 = r - 32;
+            int nN = (j + DIAMOND[k2][1]) * nx + i + DIAMOND[k2][0];
+            double di = -DIAMOND[k2][0], dj = -DIAMOND[k2][1];
+            double len = sqrt(di * di + dj * dj);
+            const om_mat* m = &M->mats[M->mat_id[d]];
+            double dir = atan2(dj, di);
+            double Vp = om_group_speed(m, M->group_model, dir, th0 + 1e-6);
+            double Vm = om_group_speed(m, M->group_model, dir, th0 - 1e-6);
+            double dT = (len * M->h / Vp - len * M->h / Vm) / 2e-6;
+            lam[nN] += lam[d];
+            grad[region[d]] += lam[d] * dT;
+        }
+    }
+    /* frozen nodes: straight-ray times from the source, orientation of the source */
+    int s = sj * nx + si;
+    const om_mat* ms = &M->mats[M->mat_id[s]];
+    for (int n = 0; n < N; ++n) {
+        if (!frozen[n] || n == s || lam[n] == 0.0) continue;
+        double di = n % nx - si, dj = n / nx - sj;
+        double dist = sqrt(di * di + dj * dj) * M->h;
+        double dir = atan2(dj, di);
+        double th = M->theta[s];
+        double dT = (dist / om_group_speed(ms, M->group_model, dir, th + 1e-6)
+                     - dist / om_group_speed(ms, M->group_model, dir, th - 1e-6)) / 2e-6;
+        grad[region[s]] += lam[n] * dT;
+    }
+    free(lam);
+    free(byrank);
+}

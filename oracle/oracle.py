@@ -89,6 +89,9 @@ def lib():
             L.om_init_hierarchy.restype = C.c_int
             L.om_init_hierarchy.argtypes = [P(Medium), C.c_int, C.c_int, C.c_int, P(C.c_int), P(C.c_int),
                                             P(C.c_uint8), P(C.c_double)]
+            L.om_adjoint.restype = None
+            L.om_adjoint.argtypes = [P(Medium), P(C.c_uint8), P(C.c_double), P(C.c_int16), P(C.c_int32),
+                                     P(C.c_double), C.c_int, C.c_int, P(C.c_int32), C.c_int, P(C.c_double)]
             L.om_trace_ray.restype = C.c_int
             L.om_trace_ray.argtypes = [P(Medium), P(C.c_double), C.c_double, C.c_double, C.c_double,
                                        C.c_double, P(RayOpts), P(C.c_double), P(C.c_int)]
@@ -244,3 +247,40 @@ def trace_ray(M: OMedium, tau, start, target, plane_step=4, halfwidth=8, stop_ra
 def path_time(M: OMedium, pts) -> float:
     p = np.ascontiguousarray(pts, np.float64).reshape(-1)
     return lib().om_path_time(C.byref(M.c), _ptr(p, C.c_double), int(p.size // 2))
+
+
+def adjoint(M: OMedium, frozen, tau, rec, order, seeds, src, region, nregions, grad=None):
+    """Reverse-mode gradient: grad[r] += dL/dtheta_r given seeds[node] = dL/dtau."""
+    fz = np.ascontiguousarray(frozen, np.uint8).reshape(-1)
+    t = np.ascontiguousarray(tau, np.float64).reshape(-1)
+    rc = np.ascontiguousarray(rec, np.int16).reshape(-1)
+    od = np.ascontiguousarray(order, np.int32).reshape(-1)
+    sd = np.ascontiguousarray(seeds, np.float64).reshape(-1)
+    rg = np.ascontiguousarray(region, np.int32).reshape(-1)
+    g = np.zeros(nregions, np.float64) if grad is None else grad
+    lib().om_adjoint(C.byref(M.c), _ptr(fz, C.c_uint8), _ptr(t, C.c_double), _ptr(rc, C.c_int16),
+                     _ptr(od, C.c_int32), _ptr(sd, C.c_double), int(src[0]), int(src[1]), _ptr(rg, C.c_int32),
+                     int(nregions), _ptr(g, C.c_double))
+    return g
+
+
+def misfit_and_gradient(wl, sample, theta, t_obs, r0=2, group_model=0):
+    """L = sum over sources and receivers of (T - T_obs)^2 and dL/dtheta (oracle), for one sample."""
+    s = wl.samples[sample]
+    mats = [mat_from_voigt(c6, rho) for c6, rho in wl.materials]
+    M = OMedium.from_regions(s.nx, s.ny, s.h, s.region_map, theta, wl.region_material, mats, group_model)
+    region = np.asarray(s.region_map, np.int32).reshape(-1)
+    L = 0.0
+    grad = np.zeros(len(theta), np.float64)
+    T = np.zeros((len(s.src), len(s.rec)))
+    for k, (si, sj) in enumerate(s.src):
+        fr, t0 = init_radius(M, si, sj, r0)
+        tau, rec, st, order = fmm(M, fr, t0, with_order=True)
+        tr = tau[s.rec[:, 1], s.rec[:, 0]]
+        T[k] = tr
+        res = tr - t_obs[k]
+        L += float(np.sum(res ** 2))
+        seeds = np.zeros(s.nx * s.ny)
+        np.add.at(seeds, s.rec[:, 1] * s.nx + s.rec[:, 0], 2.0 * res)
+        adjoint(M, fr, tau, rec, order, seeds, (si, sj), region, len(theta), grad)
+    return L, grad, T

@@ -152,6 +152,15 @@ class Plan:
                          C.c_void_p(st.data_ptr()), self._stream())
         return pts, npts, rt, st
 
+    def backward(self, theta, times, records, dL_drec):
+        """dL/dtheta [nsamples, nregions] (float64) from dL/dT at the receivers (plan needs keep_records=1)."""
+        grad = torch.empty((self.nsamples, self.nregions), dtype=torch.float64, device=self._dev())
+        g = dL_drec.to(self.dtype).contiguous()
+        B.alf_backward(self.ctx, self.plan, C.c_void_p(theta.data_ptr()), C.c_void_p(times.data_ptr()),
+                       C.c_void_p(records.data_ptr()), C.c_void_p(g.data_ptr()), C.c_void_p(grad.data_ptr()),
+                       self._stream())
+        return grad
+
     def status(self) -> int:
         return B.alf_sync_status(self.plan, self._stream())
 
@@ -169,3 +178,26 @@ def eval_velocity(c6, rho, angles, kind="phase", group="paper", precision="fp64"
                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     return out.cpu().numpy()
+
+
+class ReceiverTimes(torch.autograd.Function):
+    """Receiver travel times T[b, s, r] as a differentiable function of the region orientations theta[b, R].
+
+    forward: alf_solve (records kept); backward: alf_backward, the discrete adjoint of the solve.
+    The plan must have been created with keep_records=1."""
+
+    @staticmethod
+    def forward(ctx, theta, plan):
+        th = theta.detach().to(torch.float64).contiguous()
+        times = plan.new_times()
+        records = plan.new_records()
+        _, rt = plan.solve(th, times=times, records=records)
+        ctx.plan = plan
+        ctx.save_for_backward(th, times, records)
+        return rt
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        th, times, records = ctx.saved_tensors
+        g = ctx.plan.backward(th, times, records, grad_out)
+        return g.to(th.dtype), None

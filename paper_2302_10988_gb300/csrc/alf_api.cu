@@ -151,6 +151,10 @@ const char* alf_last_error(const alf_ctx* ctx) { return ctx ? ctx->err.c_str() :
 static void plan_free(alf_plan* p)
 {
     dfree(p->d_fields);
+    dfree(p->d_adj_w);
+    dfree(p->d_lambda);
+    dfree(p->d_gnode);
+    dfree(p->d_indeg);
     dfree(p->d_list0);
     dfree(p->d_list1);
     dfree(p->d_elist);
@@ -356,6 +360,19 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         p->d_flim = l;
     }
     ALLOC(p->d_bitmap, p->bm_words);
+    if (opt.keep_records) {
+        char* w = nullptr;
+        char* l = nullptr;
+        char* gn = nullptr;
+        const size_t tb = opt.precision == ALF_FP64 ? 8 : 4;
+        ALLOC(w, p->total_nodes * 4 * tb);
+        p->d_adj_w = w;
+        ALLOC(l, p->total_nodes * tb);
+        p->d_lambda = l;
+        ALLOC(gn, p->total_nodes * tb);
+        p->d_gnode = gn;
+        ALLOC(p->d_indeg, p->total_nodes);
+    }
     ALLOC(p->d_bm_off, (size_t)p->nfields);
     ALLOC(p->d_cnt, 2 * (size_t)p->nfields);
     ALLOC(p->d_ecnt, (size_t)p->nfields);
@@ -444,6 +461,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     const int gm = p->opt.group_model;
     ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm, p->d_regions, st));
     ALF_CUDA(ctx, launch_fill_inf(prec, times, p->total_nodes, st));
+    if (records) ALF_CUDA(ctx, cudaMemsetAsync(records, 255, p->total_nodes, st));
     ALF_CUDA(ctx, cudaMemsetAsync(p->d_frozen, 0, sizeof(unsigned) * (size_t)p->nfields * frozen_words(p->box), st));
     ALF_CUDA(ctx, launch_init_radius(prec, times, p->d_fields, p->nfields, p->d_map, p->d_region_mat, p->d_mats, theta,
                                      p->d_h, p->R, p->opt.init_radius, gm, p->d_frozen, p->box, st));
@@ -490,7 +508,8 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
         ALF_CUDA(ctx, cudaStreamSynchronize(st));
         if (*p->h_pending == 0ull) break;
     }
-    ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times, st));
+    ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times,
+                                  records, st));
     return ALF_OK;
 }
 
@@ -552,13 +571,49 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
                         const void* dL_drec, double* dL_dtheta, void* stream)
 {
     if (!p) return ALF_ERR_INVALID_ARG;
-    (void)theta;
-    (void)times;
-    (void)records;
-    (void)dL_drec;
-    (void)dL_dtheta;
-    (void)stream;
-    return fail(p->ctx, ALF_ERR_UNSUPPORTED, "alf_backward is not available in this build");
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times || !records || !dL_drec || !dL_dtheta)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: null pointer");
+    if (!p->opt.keep_records || !p->d_adj_w)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: the plan was created without keep_records");
+    if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    const int prec = p->opt.precision;
+    ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, p->opt.group_model,
+                                      p->d_regions, st));
+    AdjLaunch a;
+    a.times = times;
+    a.fields = p->d_fields;
+    a.nfields = p->nfields;
+    a.nsamples = p->B;
+    a.nrec = p->Rr;
+    a.total_nodes = p->total_nodes;
+    a.region_map = p->d_map;
+    a.region_mat = p->d_region_mat;
+    a.mats = p->d_mats;
+    a.regions = p->d_regions;
+    a.theta = theta;
+    a.h = p->d_h;
+    a.nregions = p->R;
+    a.box = p->box;
+    a.group_model = p->opt.group_model;
+    a.frozen_bits = p->d_frozen;
+    a.records = records;
+    a.rec_ij = p->d_rec;
+    a.weights = p->d_adj_w;
+    a.lambda = p->d_lambda;
+    a.gnode = p->d_gnode;
+    a.indeg = p->d_indeg;
+    a.list[0] = p->d_list0;
+    a.list[1] = p->d_list1;
+    a.cnt = p->d_cnt;
+    a.eoff = p->d_eoff;
+    long long mx = 0;
+    for (const FieldDesc& fd : p->fields) mx = std::max(mx, (long long)fd.nx * fd.ny);
+    a.max_rounds = (unsigned)std::min<long long>(mx + 64, 0x7fffffffll);
+    ALF_CUDA(ctx, launch_adjoint(prec, a, dL_drec, dL_dtheta, p->d_pending, p->h_pending, p->grid_eval, st));
+    return ALF_OK;
 }
 
 alf_status alf_sync_status(alf_plan* p, void* stream, int32_t* worst)

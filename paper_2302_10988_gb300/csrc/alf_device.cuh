@@ -22,13 +22,15 @@ namespace alf {
 // Per-(sample, region) constants of the local update.  a.. are stiffness / rho
 // (m^2/s^2) of the YZ plane; (cth, sth) the orientation; fb[c] the straight-ray
 // time over one diamond step of direction class c (x axis, y axis, diagonal
-// (1,1), diagonal (1,-1); lengths 1, 1, sqrt2, sqrt2 cells); h the spacing.
+// (1,1), diagonal (1,-1); lengths 1, 1, sqrt2, sqrt2 cells) and its
+// derivative by the orientation; h the spacing.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RegionP {
     T a22, a33, a44, a2344;
     T cth, sth;
     T fb[4];
+    T dfb[4];  // d fb / d theta (used by the adjoint)
     T h;
     int iso;
     int pad;

@@ -73,12 +73,43 @@ cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int 
                              cudaStream_t st);
 cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
-                            const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, cudaStream_t st);
+                            const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
+                            cudaStream_t st);
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
                            const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
                            const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, cudaStream_t st);
 cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
                                  double* out, int n, cudaStream_t st);
+
+// adjoint (alf_adjoint.cu)
+struct AdjLaunch {
+    const void* times;
+    const FieldDesc* fields;
+    int nfields, nsamples, nrec;
+    size_t total_nodes;
+    const uint16_t* region_map;
+    const uint16_t* region_mat;
+    const MatD* mats;
+    const void* regions;  // RegionP<T>
+    const double* theta;
+    const double* h;
+    int nregions;
+    int box;
+    int group_model;
+    const unsigned* frozen_bits;
+    const uint8_t* records;
+    const int32_t* rec_ij;
+    void* weights;    // per node: 3 support weights + orientation weight (T)
+    void* lambda;     // per node (T)
+    void* gnode;      // per node: lambda * d tau / d theta (T)
+    unsigned* indeg;  // per node
+    unsigned* list[2];
+    unsigned* cnt;    // [2][nfields]
+    unsigned* eoff;   // [nfields + 1]
+    unsigned max_rounds;
+};
+cudaError_t launch_adjoint(int precision, const AdjLaunch& a, const void* dL_drec, double* grad,
+                           unsigned long long* d_pending, unsigned long long* h_pending, int grid, cudaStream_t st);
 
 // rays (alf_ray.cu)
 struct RayLaunch {
@@ -153,6 +184,11 @@ struct alf_plan {
     unsigned long long* d_pending = nullptr;
     unsigned long long* h_pending = nullptr;  // pinned
     int rounds_per_check = 32;
+    // adjoint workspace (keep_records = 1)
+    void* d_adj_w = nullptr;
+    void* d_lambda = nullptr;
+    void* d_gnode = nullptr;
+    unsigned* d_indeg = nullptr;
     alf::QueueState* d_q = nullptr;
     unsigned* d_ray_error = nullptr;
     unsigned* d_frozen = nullptr;  // per-field bitmap of frozen nodes in the source box

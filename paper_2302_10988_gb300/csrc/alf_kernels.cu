@@ -59,7 +59,12 @@ __global__ void prep_regions_kernel(const MatD* mats, const uint16_t* region_mat
     const double kPi = 3.141592653589793;
     const double dirs[4] = {0.0, 0.5 * kPi, 0.25 * kPi, 0.75 * kPi};
     const double lens[4] = {1.0, 1.0, sqrt(2.0), sqrt(2.0)};
-    for (int cls = 0; cls < 4; ++cls) R.fb[cls] = T(lens[cls] * hb / group_speed64(m, group_model, dirs[cls] - th));
+    for (int cls = 0; cls < 4; ++cls) {
+        R.fb[cls] = T(lens[cls] * hb / group_speed64(m, group_model, dirs[cls] - th));
+        const double e = 1e-6;
+        R.dfb[cls] = T((lens[cls] * hb / group_speed64(m, group_model, dirs[cls] - th - e) -
+                        lens[cls] * hb / group_speed64(m, group_model, dirs[cls] - th + e)) / (2.0 * e));
+    }
     R.h = T(hb);
     R.iso = m.iso;
     R.pad = 0;
@@ -467,7 +472,7 @@ cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long lon
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void finalize_kernel(T* times, const FieldDesc* fields, int box, const int32_t* rec_ij, int nsrc, int nrec,
-                                T* rec_times)
+                                T* rec_times, uint8_t* records)
 {
     const int f = blockIdx.x;
     const FieldDesc fd = fields[f];
@@ -477,6 +482,7 @@ __global__ void finalize_kernel(T* times, const FieldDesc* fields, int box, cons
         const int i = fd.si + k % w - box, j = fd.sj + k / w - box;
         if (i < 0 || j < 0 || i >= fd.nx || j >= fd.ny) continue;
         T* p = tf + (long long)j * fd.nx + i;
+        if (records && neg_bit(*p)) records[fd.node_off + (long long)j * fd.nx + i] = 254;
         *p = abs_(*p);
     }
     __syncthreads();
@@ -490,14 +496,14 @@ __global__ void finalize_kernel(T* times, const FieldDesc* fields, int box, cons
 }
 
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
-                            const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, cudaStream_t st)
+                            const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records, cudaStream_t st)
 {
     if (precision == ALF_FP64)
         finalize_kernel<double><<<nfields, 256, 0, st>>>((double*)times, fields, box, rec_ij, nsrc, nrec,
-                                                         (double*)rec_times);
+                                                         (double*)rec_times, records);
     else
         finalize_kernel<float><<<nfields, 256, 0, st>>>((float*)times, fields, box, rec_ij, nsrc, nrec,
-                                                        (float*)rec_times);
+                                                        (float*)rec_times, records);
     return cudaGetLastError();
 }
 

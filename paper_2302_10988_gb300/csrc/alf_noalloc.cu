@@ -230,7 +230,8 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess && pending == 0ull) break;
     }
-    if (e == cudaSuccess) e = launch_finalize(ALF_FP32, times, d_fd, 1, init_radius, nullptr, 1, 0, nullptr, st);
+    if (e == cudaSuccess)
+        e = launch_finalize(ALF_FP32, times, d_fd, 1, init_radius, nullptr, 1, 0, nullptr, nullptr, st);
     QueueState qh{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&qh, d_q, sizeof(qh), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
