@@ -2,19 +2,22 @@
 """Benchmark of the ALI-FMM travel-time hot path on GB300.
 
 Workload (N = 1): the batched weld workload -- 512 media samples (region
-orientations drawn per sample) x 32 sources, grid sizes uniform in
-128..320 (step 32), 10 x 10 weld regions, FP32 sweeps.  One step is one pass
-of the hot path over the batch: per-region constants, near-source
-initialisation, tile sweeps to the fixed point, FP64 convergence check,
-receiver times and rays (32 receivers per source).
+orientations drawn per sample) x 32 sources, grid sizes uniform in 128..320
+(step 32), 10 x 10 weld regions, FP32.  One step is one pass of the whole hot
+path over the batch: per-region constants, near-source initialisation, the
+sweep to the fixed point (rounds replayed from a CUDA graph), receiver times,
+the FP64 convergence check, rays for 32 receivers per source and the adjoint
+gradient of a receiver-time misfit with respect to the region orientations.
 
-Metric: travel-time nodes/s = sum over fields of nx*ny / step time.
+Metric: travel-time nodes/s = sum over fields of nx * ny / step time.  Also
+reported: the plain single-medium form (256 x 256, 32 sources, FP32 and FP64)
+and the gradient time of the 256-sample adjoint workload (200 x 200).
 Inputs are synthetic and seeded; the packed fields (3.6 GB FP32) are larger
 than L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-With N > 1 (launched by torchrun) every rank solves its own share of the
-samples (no collective on the data path) and rank 0 prints the line.
+With N > 1 (launched by torchrun) every rank solves its own copy of the batch
+(weak scaling, no collective on the data path) and rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -32,46 +35,48 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "travel-time nodes/s (sources x models x nodes), batched FP32"
-WORKLOAD = "weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 regions, FP32"
+WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 regions, FP32; "
+            "step = solve + FP64 check + 32 rays/source + adjoint gradient")
+# algorithmic FP32-pipe operations of one evaluation of the local operator (derivation in the design doc)
+OPS_PER_EVAL = 627.0
+SMS, FP32_LANES = 152, 128
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=512)
-    ap.add_argument("--no-rays", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain and gradient side measurements")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: direct launches on the default stream, no autotune, one warm-up step and "
+                         "one step, a short summary line (for ncu)")
     return ap.parse_args()
 
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
-        self.index = index
-        self.rows = []
-        self.proc = None
+        self.index, self.rows, self.proc = index, [], None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
 
@@ -87,17 +92,13 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        reasons = set()
+        ok = [r for r in self.rows if len(r) >= 9]
+        sm = [float(r[1]) for r in ok if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in ok if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) >= 9:
-                for k, n in enumerate(names):
-                    if r[5 + k].lower().startswith("active"):
-                        reasons.add(n)
+        reasons = sorted({n for r in ok for k, n in enumerate(names) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons}
 
 
 def _peaks():
@@ -108,21 +109,16 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 issue roofline of the ALU-bound sweep: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
-SMS, FP32_LANES = 152, 128
-
-
 def cpu_baseline(wl, seconds=12.0):
-    """The FP64 oracle (heap FMM, as it stands) on a bounded sample of the workload's fields, timed on the
-    host cores with one thread per field (ctypes releases the GIL)."""
+    """The FP64 oracle (heap FMM, as it stands) on a bounded sample of the workload's fields, timed on the host
+    cores with one thread per field (ctypes releases the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import oracle as O
     O.build()
     mats = [O.mat_from_voigt(c6, rho) for c6, rho in wl.materials]
     fields = [(b, s) for b in range(len(wl.samples)) for s in range(len(wl.samples[b].src))]
-    rng = np.random.default_rng(0)
-    order = rng.permutation(len(fields))
+    order = np.random.default_rng(0).permutation(len(fields))
     cores = os.cpu_count() or 1
 
     def one(k):
@@ -141,7 +137,7 @@ def cpu_baseline(wl, seconds=12.0):
             nf += cores
     dt = time.perf_counter() - t0
     return {"value": nodes / dt, "unit": "nodes/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nf} of {len(fields)} fields (FP64 heap FMM, radius-2 init), {dt:.1f} s"}
+            "sample": f"{nf} of {len(fields)} fields, FP64 heap FMM (solve only), {dt:.1f} s on {cores} threads"}
 
 
 def run_reference(args):
@@ -150,20 +146,33 @@ def run_reference(args):
         return
     from paper_2302_10988_gb300 import workloads as W
     wl = W.weld_batch(nsamples=args.samples)
-    vals = []
     for _ in range(args.warmup):
         cpu_baseline(wl, seconds=2.0)
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(wl, seconds=6.0))
+    vals = [cpu_baseline(wl, seconds=6.0) for _ in range(args.steps)]
     v = float(np.mean([x["value"] for x in vals]))
-    total = wl.nodes()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nodes/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "fields larger than L2"},
-            "cpu_baseline": dict(vals[-1], value=v),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.nodes() / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": dict(vals[-1], value=v),
             "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def profile_run(args, wl, api, local):
+    """One warm-up step and one step of the hot path with direct launches (no CUDA graph) on the default stream."""
+    import torch
+    P = api.Plan(wl, precision="fp32", device=local, keep_records=1, use_graph=0, band_cells=2.0)
+    th = P.theta_tensor()
+    times, rect, rec = P.new_times(), P.new_rec_times(), P.new_records()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        P.solve(th, times=times, rec_times=rect, records=rec)
+        P.check64(th, times, rec)
+        P.trace_rays(th, times)
+        P.backward(th, times, rec, 2.0 * rect)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": True, "fields": P.nfields, "nodes": P.total_nodes, "status": P.status(),
+                      "seconds": time.perf_counter() - t0}), flush=True)
 
 
 def main():
@@ -181,104 +190,169 @@ def main():
     __graft_entry__.build()
     from paper_2302_10988_gb300 import api, workloads as W
 
-    wl_all = W.weld_batch(nsamples=args.samples)
-    # weak scaling: every rank takes its own samples (the whole batch per rank)
-    wl = wl_all
-    P = api.Plan(wl, precision="fp32", device=local)
+    wl = W.weld_batch(nsamples=args.samples)
+    if args.profile:
+        return profile_run(args, wl, api, local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    P = api.Plan(wl, precision="fp32", device=local, keep_records=1)
     th = P.theta_tensor()
-    times = P.new_times()
-    rect = P.new_rec_times()
-    rec = P.new_records()
-    max_rel = flips = None
-    stream = torch.cuda.current_stream()
+    times, rect, rec = P.new_times(), P.new_rec_times(), P.new_records()
+    P.autotune(th, times, rec)
+    # observed times: a solve at perturbed orientations plus 10 ns noise (inputs of the adjoint)
+    th_obs = P.theta_tensor(np.stack([s.region_theta for s in wl.samples]) + 0.05)
+    _, t_obs = P.solve(th_obs)
+    t_obs = (t_obs + 1e-8 * torch.randn_like(t_obs)).contiguous()
 
-    def step():
-        nonlocal max_rel, flips
-        P.solve(th, times=times, rec_times=rect, records=rec)
-        max_rel, flips = P.check64(th, times, rec)
-        if not args.no_rays:
-            P.trace_rays(th, times)
+    stage = {}
+
+    def step(theta, timed_stages=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timed_stages else None
+        if ev: ev[0].record(stream)
+        P.solve(theta, times=times, rec_times=rect, records=rec)
+        if ev: ev[1].record(stream)
+        mr, fl = P.check64(theta, times, rec)
+        if ev: ev[2].record(stream)
+        P.trace_rays(theta, times)
+        if ev: ev[3].record(stream)
+        g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
+        if ev:
+            ev[4].record(stream)
+            torch.cuda.synchronize()
+            for k, name in enumerate(["solve", "check64", "rays", "adjoint"]):
+                stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
+        return mr, fl, g
 
     for _ in range(max(args.warmup, 3)):
-        step()
-    code = P.status()
-    if code != 0:
-        raise SystemExit(f"device status {code} during warm-up")
-    stats = P.stats()
+        step(th)
+    if P.status() != 0:
+        raise SystemExit("device status non-zero during warm-up")
 
-    # sweep-kernel share of the step, timed on the launching stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(2):
-        P.solve(th, times=times, rec_times=rect, records=rec)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    solve_ms = e0.elapsed_time(e1) / 2
-
+    # ---- timed region (headline): whole step, sweep rounds from CUDA graphs
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    launches0 = P.stats()["kernel_launches"]
     clocks.start()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for _ in range(args.steps):
-        step()
+        mr, fl, g = step(th)
     end.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
+    launches = (P.stats()["kernel_launches"] - launches0) // args.steps
     ms = start.elapsed_time(end) / args.steps
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    code = P.status()
-    if code != 0:
-        raise SystemExit(f"device status {code} in the timed region")
+    if P.status() != 0:
+        raise SystemExit("device status non-zero in the timed region")
     nodes = P.total_nodes * world
     value = nodes / (ms * 1e-3)
+    for _ in range(args.steps):
+        step(th, timed_stages=True)
+    stage = {k: v / args.steps for k, v in stage.items()}
 
-    # end to end: orientations from pinned host memory, receiver times back to the host
+    # ---- roofline of the dominant kernel (the evaluation of the local operator): its launches timed with
+    # CUDA events on the solve's stream, over a second run of the same solves
+    Pt = api.Plan(wl, precision="fp32", device=local, time_kernels=1, band_cells=P.options.band_cells)
+    tt = Pt.new_times()
+    Pt.solve(th, times=tt)
+    ev_ms, evals, eval_launches = 0.0, 0, 0
+    for _ in range(args.steps):
+        Pt.solve(th, times=tt)
+        s = Pt.stats()
+        ev_ms += s["eval_ms"]
+        evals += s["evaluations"]
+        eval_launches += s["eval_launches"]
+    peaks, peak_kind = _peaks()
+    clock = ck["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    achieved = OPS_PER_EVAL * evals / (ev_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * clock * 1e6 / 1e12
+    evals_per_node = evals / (args.steps * P.total_nodes)
+    del Pt, tt
+
+    # ---- end to end through the public API: orientations from pinned host memory, receiver times back
     th_host = torch.from_numpy(np.stack([s.region_theta for s in wl.samples])).pin_memory()
     rt_host = torch.empty(rect.shape, dtype=rect.dtype).pin_memory()
+    g_host = torch.empty(th.shape, dtype=torch.float64).pin_memory()
     th_dev = torch.empty_like(th)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         th_dev.copy_(th_host, non_blocking=True)
-        P.solve(th_dev, times=times, rec_times=rect, records=rec)
-        P.check64(th_dev, times, rec)
-        if not args.no_rays:
-            P.trace_rays(th_dev, times)
+        _, _, g = step(th_dev)
         rt_host.copy_(rect, non_blocking=True)
+        g_host.copy_(g, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    torch.cuda.synchronize()
-    peaks, peak_kind = _peaks()
-    clock = ck["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    # ALU roofline of the sweep: algorithmic FP32 flops per node x nodes / solve time
-    flops_per_node = float(os.environ.get("ALF_FLOPS_PER_NODE", "0")) or None
-    achieved = (flops_per_node * P.total_nodes / (solve_ms * 1e-3) / 1e12) if flops_per_node else None
-    peak = SMS * FP32_LANES * 2 * clock * 1e6 / 1e12
+
     line = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fields": P.nfields, "nodes_per_step": P.total_nodes,
-                   "rays_per_step": 0 if args.no_rays else P.nfields * P.nrec, "cta_threads": P.options.cta_threads,
+                   "rays_per_step": P.nfields * P.nrec, "band_cells": P.options.band_cells,
                    "l2": "inputs larger than L2 (3.6 GB of fields), no flush"},
-        "solve_ms": solve_ms, "evaluations_per_node": stats["evaluations"] / max(stats["nodes"], 1),
-        "fp64_check": {"max_rel_residual": float(max_rel.max().item()), "record_flips": int(flips.sum().item())},
+        "stage_ms": stage, "evaluations_per_node": evals_per_node,
+        "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},
         "e2e": {"value": nodes / (e2e_ms * 1e-3), "unit": "nodes/s",
-                "h2d_bytes_per_step": int(th_host.numel() * 8),
-                "d2h_bytes_per_step": int(rt_host.numel() * rt_host.element_size())},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock:.0f} MHz (sampled clock)"},
+                "h2d_bytes_per_step": int(th_host.numel() * th_host.element_size()),
+                "d2h_bytes_per_step": int(rt_host.numel() * rt_host.element_size()
+                                          + g_host.numel() * g_host.element_size())},
+        "roofline": {"bound": "alu", "kernel": "fim_eval_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {clock:.0f} MHz (sampled clock); "
+                                    f"{OPS_PER_EVAL:.0f} FP32 ops per evaluation",
+                     "avg_launch_ms": ev_ms / max(eval_launches, 1), "launches": eval_launches // args.steps},
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
     }
+    if not args.quick:
+        # plain single-medium form: 256 x 256 weld, 32 sources
+        wl1 = W.weld_single()
+        plain = {}
+        for prec in ("fp32", "fp64"):
+            P1 = api.Plan(wl1, precision=prec, device=local)
+            th1 = P1.theta_tensor()
+            t1 = P1.new_times()
+            P1.solve(th1, times=t1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                P1.solve(th1, times=t1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain[prec] = P1.total_nodes / (e0.elapsed_time(e1) / 3 * 1e-3)
+            del P1, t1
+        line["plain_nodes_per_s"] = plain
+        # gradient: 256 samples x 32 sources on 200 x 200, forward (records) + adjoint
+        wl3, truth = W.weld_adjoint()
+        P3 = api.Plan(wl3, precision="fp32", device=local, keep_records=1)
+        th3 = P3.theta_tensor()
+        Pt3 = api.Plan(truth, precision="fp32", device=local)
+        _, tob = Pt3.solve(Pt3.theta_tensor())
+        tob = (tob + torch.as_tensor(W.observation_noise(tuple(tob.shape)), device=tob.device).float())
+        t3, r3, c3 = P3.new_times(), P3.new_rec_times(), P3.new_records()
+
+        def grad_step():
+            P3.solve(th3, times=t3, rec_times=r3, records=c3)
+            return P3.backward(th3, t3, c3, 2.0 * (r3 - tob))
+        grad_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            grad_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["grad_ms"] = e0.elapsed_time(e1) / 3
+        line["grad_config"] = "256 samples x 32 sources x 32 receivers, 200 x 200, FP32 forward + adjoint"
+        del P3, Pt3
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

@@ -107,6 +107,8 @@ typedef struct {
     int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
     double band_cells;      /* sweep schedule: nodes later than the front by more than this many
                                cell-crossing times wait for the front (default 4; <= 0: no band) */
+    int use_graph;          /* 1: replay the sweep rounds from a CUDA graph (default 1) */
+    int time_kernels;       /* 1: time the evaluation kernel with CUDA events (alf_plan_stats; default 0) */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */
@@ -220,10 +222,23 @@ alf_status alf_backward(alf_plan* plan, const double* region_theta, const void* 
  * matching alf_status as the return value. */
 alf_status alf_sync_status(alf_plan* plan, void* stream, int32_t* worst);
 
-/* Work counters of the last alf_solve on `stream` (synchronises `stream`):
- *  out[0] node evaluations of the sweep kernel, out[1] sweep rounds over all
- *  fields, out[2] nodes in the plan, out[3] persistent CTAs launched. */
-alf_status alf_plan_stats(alf_plan* plan, void* stream, uint64_t out[4]);
+/* Work counters of the last alf_solve (synchronises `stream`). */
+typedef struct {
+    uint64_t node_evaluations; /* evaluations of the local operator in the sweep */
+    uint64_t rounds;           /* sweep rounds */
+    uint64_t nodes;            /* nodes of the plan */
+    uint64_t eval_launches;    /* evaluation-kernel launches timed (option time_kernels = 1) */
+    double eval_ms;            /* their device time, measured with CUDA events on the solve's stream */
+    uint64_t kernel_launches;  /* kernel launches issued by the library so far (whole process) */
+} alf_stats;
+alf_status alf_plan_stats(alf_plan* plan, void* stream, alf_stats* out);
+
+/* Picks the sweep's launch parameters for this plan by timing full solves
+ * of its batch (the front band width 2, 3, 4 or 6 cells and the evaluation
+ * CTA size 128 or 256 threads) and keeps the fastest; `times` and
+ * `records` (may be NULL) are scratch outputs of those solves.  Synchronous. */
+alf_status alf_plan_autotune(alf_plan* plan, const double* region_theta, void* times, uint8_t* records,
+                             void* stream);
 
 /* Velocity model on the device, for checks: out[k] = qP phase speed (kind 0)
  * or group speed (kind 1, model `group_model`) of material *mat (host) at

@@ -40,8 +40,8 @@ class Plan:
     """A batch of fields (samples x sources) of one workload, ready to solve.
 
     Keyword options map to ``alf_options`` fields (precision "fp32"/"fp64",
-    group "paper"/"exact", init_radius, cta_threads, ctas_per_sm, plane_step,
-    ray_halfwidth, stop_radius, max_ray_points, max_rounds, keep_records)."""
+    group "paper"/"exact", init_radius, plane_step, ray_halfwidth, stop_radius,
+    max_ray_points, max_rounds, keep_records, band_cells, use_graph, time_kernels)."""
 
     def __init__(self, wl, precision="fp32", group="paper", device=0, **opts):
         self.wl = wl
@@ -166,6 +166,13 @@ class Plan:
 
     def stats(self) -> dict:
         return B.alf_plan_stats(self.ctx, self.plan, self._stream())
+
+    def autotune(self, theta, times=None, records=None):
+        times = self.new_times() if times is None else times
+        B.alf_plan_autotune(self.ctx, self.plan, C.c_void_p(theta.data_ptr()), C.c_void_p(times.data_ptr()),
+                            C.c_void_p(records.data_ptr()) if records is not None else None, self._stream())
+        self.options = B.alf_plan_options(self.plan)
+        return self.options
 
 
 def eval_velocity(c6, rho, angles, kind="phase", group="paper", precision="fp64", device=0):

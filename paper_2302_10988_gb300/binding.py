@@ -25,7 +25,7 @@ ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
 # every symbol include/alifmm.h declares
 EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error", "alf_plan_create",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
-           "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats",
+           "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats", "alf_plan_autotune",
            "alf_eval_velocity", "alf_solve_field_noalloc")
 
 
@@ -44,7 +44,13 @@ class alf_options(C.Structure):
                 ("n_levels", C.c_int), ("level_density", C.c_int * 4), ("level_radius", C.c_int * 4),
                 ("plane_step", C.c_int), ("ray_halfwidth", C.c_int), ("stop_radius", C.c_double),
                 ("max_ray_points", C.c_int), ("max_rounds", C.c_int), ("cta_threads", C.c_int),
-                ("ctas_per_sm", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double)]
+                ("ctas_per_sm", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double),
+                ("use_graph", C.c_int), ("time_kernels", C.c_int)]
+
+
+class alf_stats(C.Structure):
+    _fields_ = [("node_evaluations", C.c_uint64), ("rounds", C.c_uint64), ("nodes", C.c_uint64),
+                ("eval_launches", C.c_uint64), ("eval_ms", C.c_double), ("kernel_launches", C.c_uint64)]
 
 
 class alf_geometry(C.Structure):
@@ -99,7 +105,9 @@ def load(path: str = LIB_PATH):
         L.alf_sync_status.restype = C.c_int
         L.alf_sync_status.argtypes = [vp, vp, P(C.c_int32)]
         L.alf_plan_stats.restype = C.c_int
-        L.alf_plan_stats.argtypes = [vp, vp, P(C.c_uint64)]
+        L.alf_plan_stats.argtypes = [vp, vp, P(alf_stats)]
+        L.alf_plan_autotune.restype = C.c_int
+        L.alf_plan_autotune.argtypes = [vp, vp, vp, vp, vp]
         L.alf_solve_field_noalloc.restype = C.c_int
         L.alf_solve_field_noalloc.argtypes = [C.c_int, P(alf_material), C.c_int, vp, C.c_int, vp, vp, C.c_int,
                                               C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
@@ -186,9 +194,15 @@ def alf_sync_status(plan, stream) -> int:
 
 
 def alf_plan_stats(ctx, plan, stream):
-    out = (C.c_uint64 * 4)()
-    _check(ctx, load().alf_plan_stats(plan, stream, out))
-    return {"evaluations": int(out[0]), "rounds": int(out[1]), "nodes": int(out[2]), "ctas": int(out[3])}
+    out = alf_stats()
+    _check(ctx, load().alf_plan_stats(plan, stream, C.byref(out)))
+    return {"evaluations": int(out.node_evaluations), "rounds": int(out.rounds), "nodes": int(out.nodes),
+            "eval_launches": int(out.eval_launches), "eval_ms": float(out.eval_ms),
+            "kernel_launches": int(out.kernel_launches)}
+
+
+def alf_plan_autotune(ctx, plan, theta_ptr, times_ptr, records_ptr, stream):
+    _check(ctx, load().alf_plan_autotune(plan, theta_ptr, times_ptr, records_ptr, stream))
 
 
 def alf_eval_velocity(ctx, mat: alf_material, kind, group_model, precision, angles_ptr, out_ptr, n, stream):

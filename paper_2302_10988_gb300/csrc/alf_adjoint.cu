@@ -319,6 +319,7 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
     adj_weights_kernel<T><<<grid, 256, 0, st>>>(a);
     adj_seed_kernel<T><<<64, 256, 0, st>>>(a, (const T*)dL_drec);
     adj_frontier_kernel<<<std::max(1, std::min((a.nfields + 7) / 8, grid)), 256, 0, st>>>(a);
+    note_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int parity = 0;
     for (long long r = 0; r < (long long)a.max_rounds;) {
@@ -328,10 +329,12 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
                 cudaSuccess)
                 return e;
             adj_process_kernel<T><<<grid, 256, 0, st>>>(a, parity);
+            note_launches(2);
             parity ^= 1;
         }
         if ((e = cudaMemsetAsync(d_pending, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
         adj_pending_kernel<<<64, 256, 0, st>>>(a, parity, d_pending);
+        note_launches(1);
         if ((e = cudaMemcpyAsync(h_pending, d_pending, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess)
             return e;
@@ -340,6 +343,7 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
     }
     const size_t smem = a.nregions <= 4096 ? (size_t)a.nregions * sizeof(double) : 0;
     adj_reduce_kernel<T><<<a.nfields, 256, smem, st>>>(a, grad);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -74,6 +74,82 @@ size_t next_pow2(size_t v)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+
+// The sweep rounds until every dirty set is empty.  Rounds are issued in
+// chunks of rounds_per_check (an even number, so every chunk starts at parity
+// 0); after each chunk the remaining work is read back.  A chunk is replayed
+// from a CUDA graph captured for the current output pointers, unless the
+// evaluation kernel is being timed.
+alf_status run_sweep(alf_plan* p, const FimLaunch& a, cudaStream_t st)
+{
+    alf_ctx* ctx = p->ctx;
+    const int prec = p->opt.precision;
+    long long max_total = 0;
+    for (const FieldDesc& fd : p->fields) max_total = std::max(max_total, (long long)(fd.nx + fd.ny));
+    max_total *= p->opt.max_rounds;
+    const bool timing = p->opt.time_kernels != 0;
+    // stream capture is not possible on the legacy default stream: launch directly there
+    const bool graph = p->opt.use_graph != 0 && !timing && st != nullptr && st != cudaStreamLegacy &&
+                       st != cudaStreamPerThread;
+    if (timing && p->ev.empty()) {
+        p->ev.resize(2 * (size_t)p->rounds_per_check);
+        for (auto& e : p->ev) ALF_CUDA(ctx, cudaEventCreate(&e));
+    }
+    p->eval_ms = 0.0;
+    p->eval_launches = 0;
+    p->sweep_rounds = 0;
+    if (graph && (p->chunk_graph == nullptr || p->graph_times != a.times || p->graph_records != a.records)) {
+        if (p->chunk_graph) {
+            cudaGraphExecDestroy(p->chunk_graph);
+            p->chunk_graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        ALF_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (int k = 0; k < p->rounds_per_check && ce == cudaSuccess; ++k)
+            ce = launch_fim_round(prec, a, k & 1, p->grid_fields, p->grid_eval, st, p->eval_block);
+        if (ce == cudaSuccess) ce = launch_fim_pending(a, 0, p->d_pending, st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(p->h_pending, p->d_pending, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(ctx, ALF_ERR_CUDA, "sweep graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        ee = cudaGraphInstantiate(&p->chunk_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ee != cudaSuccess) return fail(ctx, ALF_ERR_CUDA, "sweep graph: %s", cudaGetErrorString(ee));
+        p->graph_times = a.times;
+        p->graph_records = a.records;
+    }
+    for (long long r = 0; r < max_total;) {
+        if (graph) {
+            ALF_CUDA(ctx, cudaGraphLaunch(p->chunk_graph, st));
+            note_launches((unsigned)p->rounds_per_check * 4 + 1);
+            r += p->rounds_per_check;
+        } else {
+            for (int k = 0; k < p->rounds_per_check; ++k, ++r) {
+                cudaEvent_t e0 = timing ? p->ev[2 * k] : nullptr, e1 = timing ? p->ev[2 * k + 1] : nullptr;
+                ALF_CUDA(ctx, launch_fim_round(prec, a, k & 1, p->grid_fields, p->grid_eval, st, p->eval_block, e0, e1));
+            }
+            ALF_CUDA(ctx, launch_fim_pending(a, 0, p->d_pending, st));
+            ALF_CUDA(ctx, cudaMemcpyAsync(p->h_pending, p->d_pending, sizeof(unsigned long long),
+                                          cudaMemcpyDeviceToHost, st));
+        }
+        ALF_CUDA(ctx, cudaStreamSynchronize(st));
+        p->sweep_rounds += (unsigned long long)p->rounds_per_check;
+        if (timing)
+            for (int k = 0; k < p->rounds_per_check; ++k) {
+                float ms = 0.f;
+                ALF_CUDA(ctx, cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]));
+                p->eval_ms += ms;
+                p->eval_launches++;
+            }
+        if (*p->h_pending == 0ull) break;
+    }
+    return ALF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -102,6 +178,8 @@ void alf_default_options(alf_options* o)
     o->ctas_per_sm = 0;
     o->keep_records = 0;
     o->band_cells = 4.0;
+    o->use_graph = 1;
+    o->time_kernels = 0;
 }
 
 alf_status alf_create(alf_ctx** out, int cuda_device)
@@ -150,6 +228,8 @@ const char* alf_last_error(const alf_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 static void plan_free(alf_plan* p)
 {
+    if (p->chunk_graph) cudaGraphExecDestroy(p->chunk_graph);
+    for (auto& e : p->ev) cudaEventDestroy(e);
     dfree(p->d_fields);
     dfree(p->d_adj_w);
     dfree(p->d_lambda);
@@ -492,21 +572,9 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     a.q = p->d_q;
     a.records = records;
     ALF_CUDA(ctx, launch_fim_init(prec, a, p->grid_fields, st));
-    // rounds until every dirty set is empty; the work left is read back every
-    // rounds_per_check rounds (rounds of finished fields exit immediately)
-    long long max_total = 0;
-    for (const FieldDesc& fd : p->fields) max_total = std::max(max_total, (long long)(fd.nx + fd.ny));
-    max_total *= p->opt.max_rounds;
-    int parity = 0;
-    for (long long r = 0; r < max_total;) {
-        for (int k = 0; k < p->rounds_per_check; ++k, ++r) {
-            ALF_CUDA(ctx, launch_fim_round(prec, a, parity, p->grid_fields, p->grid_eval, st));
-            parity ^= 1;
-        }
-        ALF_CUDA(ctx, launch_fim_pending(a, parity, p->d_pending, st));
-        ALF_CUDA(ctx, cudaMemcpyAsync(p->h_pending, p->d_pending, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        ALF_CUDA(ctx, cudaStreamSynchronize(st));
-        if (*p->h_pending == 0ull) break;
+    {
+        const alf_status rc = run_sweep(p, a, st);
+        if (rc != ALF_OK) return rc;
     }
     ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times,
                                   records, st));
@@ -638,20 +706,71 @@ alf_status alf_sync_status(alf_plan* p, void* stream, int32_t* worst)
     return ALF_OK;
 }
 
-alf_status alf_plan_stats(alf_plan* p, void* stream, uint64_t out[4])
+alf_status alf_plan_stats(alf_plan* p, void* stream, alf_stats* out)
 {
     if (!p || !out) return ALF_ERR_INVALID_ARG;
     alf_ctx* ctx = p->ctx;
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);
-    QueueState q;
     ALF_CUDA(ctx, cudaMemcpyAsync(p->h_q, p->d_q, sizeof(QueueState), cudaMemcpyDeviceToHost, st));
     ALF_CUDA(ctx, cudaStreamSynchronize(st));
-    q = *p->h_q;
-    out[0] = q.visits;
-    out[1] = q.rounds;
-    out[2] = (uint64_t)p->total_nodes;
-    out[3] = (uint64_t)p->grid_eval;
+    out->node_evaluations = p->h_q->visits;
+    out->rounds = p->sweep_rounds;
+    out->nodes = (uint64_t)p->total_nodes;
+    out->eval_launches = p->eval_launches;
+    out->eval_ms = p->eval_ms;
+    out->kernel_launches = launches_so_far();
+    return ALF_OK;
+}
+
+alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint8_t* records, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_plan_autotune: null theta or times");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    const double bands[4] = {2.0, 3.0, 4.0, 6.0};
+    const int blocks[2] = {128, 256};
+    double best_ms = 1e30, best_band = p->opt.band_cells;
+    int best_block = p->eval_block;
+    cudaEvent_t e0, e1;
+    ALF_CUDA(ctx, cudaEventCreate(&e0));
+    ALF_CUDA(ctx, cudaEventCreate(&e1));
+    const int keep_timing = p->opt.time_kernels;
+    p->opt.time_kernels = 0;
+    for (double band : bands)
+        for (int blk : blocks) {
+            p->opt.band_cells = band;
+            p->eval_block = blk;
+            if (p->chunk_graph) {
+                cudaGraphExecDestroy(p->chunk_graph);
+                p->chunk_graph = nullptr;
+            }
+            alf_status rc = alf_solve(p, theta, times, nullptr, records, stream);  // graph capture run
+            if (rc != ALF_OK) return rc;
+            ALF_CUDA(ctx, cudaEventRecord(e0, st));
+            rc = alf_solve(p, theta, times, nullptr, records, stream);
+            if (rc != ALF_OK) return rc;
+            ALF_CUDA(ctx, cudaEventRecord(e1, st));
+            ALF_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ALF_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_band = band;
+                best_block = blk;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->opt.band_cells = best_band;
+    p->eval_block = best_block;
+    p->opt.time_kernels = keep_timing;
+    if (p->chunk_graph) {
+        cudaGraphExecDestroy(p->chunk_graph);
+        p->chunk_graph = nullptr;
+    }
     return ALF_OK;
 }
 

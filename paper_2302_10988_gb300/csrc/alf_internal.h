@@ -70,7 +70,11 @@ cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fiel
                                unsigned* frozen_bits, int box, cudaStream_t st);
 cudaError_t launch_fim_init(int precision, const FimLaunch& a, int grid_fields, cudaStream_t st);
 cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int grid_fields, int grid_eval,
-                             cudaStream_t st);
+                             cudaStream_t st, int eval_block = 128, cudaEvent_t ev0 = nullptr,
+                             cudaEvent_t ev1 = nullptr);
+// kernel launches issued by this library so far (all plans, all devices)
+void note_launches(unsigned n);
+unsigned long long launches_so_far();
 cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
@@ -184,6 +188,16 @@ struct alf_plan {
     unsigned long long* d_pending = nullptr;
     unsigned long long* h_pending = nullptr;  // pinned
     int rounds_per_check = 32;
+    int eval_block = 128;           // threads per CTA of the evaluation step (autotuned)
+    // CUDA graph of one chunk of rounds, for the pointers it was captured with
+    cudaGraphExec_t chunk_graph = nullptr;
+    const void* graph_times = nullptr;
+    const void* graph_records = nullptr;
+    const void* graph_regions = nullptr;
+    // evaluation-kernel timing (alf_plan_stats)
+    std::vector<cudaEvent_t> ev;
+    double eval_ms = 0.0;
+    unsigned long long eval_launches = 0, sweep_rounds = 0;
     // adjoint workspace (keep_records = 1)
     void* d_adj_w = nullptr;
     void* d_lambda = nullptr;

@@ -8,11 +8,16 @@
 //                 fixed point, all fields of the batch in every round
 //  finalize       clears the frozen marks and gathers receiver times
 //  check64        FP64 evaluation of F at every node of a solved field
+#include <atomic>
 #include <cstdio>
 
 #include "alf_internal.h"
 
 namespace alf {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned n) { g_launches += n; }
+unsigned long long launches_so_far() { return g_launches.load(); }
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -83,6 +88,7 @@ cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t*
     else
         prep_regions_kernel<float><<<gs, bs, 0, st>>>(mats, region_mat, theta, h, nsamples, nregions, group_model,
                                                       (RegionP<float>*)regions_out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -113,6 +119,7 @@ cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t s
     if (grid < 1) grid = 1;
     if (precision == ALF_FP64) fill_inf_kernel<double><<<grid, 256, 0, st>>>((double*)times, n);
     else fill_inf_kernel<float><<<grid, 256, 0, st>>>((float*)times, n);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -157,6 +164,7 @@ cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fiel
     else
         init_radius_kernel<float><<<nfields, 128, 0, st>>>((float*)times, fields, region_map, region_mat, mats, theta,
                                                            h, nregions, r0, group_model, frozen_bits, box);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -305,7 +313,7 @@ __global__ void fim_prep_kernel(FimLaunch a, int parity)
         }
         pending += nact;
     }
-    if (lane == 0 && pending) atomicAdd(&a.q->visits, pending);
+    (void)pending;
 }
 
 // exclusive scan of the per-field evaluation counts (one block)
@@ -330,7 +338,10 @@ __global__ void fim_scan_kernel(FimLaunch a)
         a.eoff[f] = run;
         run += a.ecnt[f];
     }
-    if (threadIdx.x == 1023) a.eoff[n] = s[1023];
+    if (threadIdx.x == 1023) {
+        a.eoff[n] = s[1023];
+        if (s[1023]) atomicAdd(&a.q->visits, (unsigned long long)s[1023]);
+    }
 }
 
 ALF_D int field_of(const unsigned* eoff, int nfields, unsigned e)
@@ -343,8 +354,8 @@ ALF_D int field_of(const unsigned* eoff, int nfields, unsigned e)
     return lo;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) fim_eval_kernel(FimLaunch a)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) fim_eval_kernel(FimLaunch a)
 {
     const unsigned E = a.eoff[a.nfields];
     T* times = (T*)a.times;
@@ -436,12 +447,17 @@ __global__ void fim_pending_kernel(FimLaunch a, int parity, unsigned long long* 
 }
 
 template <typename T>
-static cudaError_t fim_round_t(const FimLaunch& a, int parity, int grid_fields, int grid_eval, cudaStream_t st)
+static cudaError_t fim_round_t(const FimLaunch& a, int parity, int grid_fields, int grid_eval, int eval_block,
+                               cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t st)
 {
     fim_prep_kernel<T><<<grid_fields, 256, 0, st>>>(a, parity);
     fim_scan_kernel<<<1, 1024, 0, st>>>(a);
-    fim_eval_kernel<T><<<grid_eval, 128, 0, st>>>(a);
+    if (ev0) cudaEventRecord(ev0, st);
+    if (eval_block == 256) fim_eval_kernel<T, 256><<<grid_eval / 2, 256, 0, st>>>(a);
+    else fim_eval_kernel<T, 128><<<grid_eval, 128, 0, st>>>(a);
+    if (ev1) cudaEventRecord(ev1, st);
     fim_mark_kernel<T><<<grid_eval, 256, 0, st>>>(a, parity);
+    note_launches(4);
     return cudaGetLastError();
 }
 
@@ -449,14 +465,15 @@ cudaError_t launch_fim_init(int precision, const FimLaunch& a, int grid_fields, 
 {
     if (precision == ALF_FP64) fim_init_kernel<double><<<grid_fields, 256, 0, st>>>(a);
     else fim_init_kernel<float><<<grid_fields, 256, 0, st>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int grid_fields, int grid_eval,
-                             cudaStream_t st)
+                             cudaStream_t st, int eval_block, cudaEvent_t ev0, cudaEvent_t ev1)
 {
-    return precision == ALF_FP64 ? fim_round_t<double>(a, parity, grid_fields, grid_eval, st)
-                                 : fim_round_t<float>(a, parity, grid_fields, grid_eval, st);
+    return precision == ALF_FP64 ? fim_round_t<double>(a, parity, grid_fields, grid_eval, eval_block, ev0, ev1, st)
+                                 : fim_round_t<float>(a, parity, grid_fields, grid_eval, eval_block, ev0, ev1, st);
 }
 
 cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st)
@@ -464,6 +481,7 @@ cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long lon
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     fim_pending_kernel<<<64, 256, 0, st>>>(a, parity, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -504,6 +522,7 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
     else
         finalize_kernel<float><<<nfields, 256, 0, st>>>((float*)times, fields, box, rec_ij, nsrc, nrec,
                                                         (float*)rec_times, records);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -519,6 +538,12 @@ ALF_D bool box_frozen(const unsigned* bits, int box, const FieldDesc& fd, int i,
     return (bits[bit >> 5] >> (bit & 31)) & 1u;
 }
 
+// At a fixed point, F at D reads exactly the neighbours that precede D in key
+// order, so the check evaluates in FP64 the update U of that known set: pair
+// metrics and feasibility for all 16 pairs, then the time of the best usable
+// pair only (lazily: the next best when a pair is not usable), else the
+// fallback.  The FP64 work per node is a few dozen operations plus one or two
+// stencil times.
 template <typename T>
 __global__ void check64_kernel(const T* times, const FieldDesc* fields, const uint16_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
@@ -536,21 +561,68 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, const ui
     for (int me = blockIdx.x * blockDim.x + threadIdx.x; me < n; me += gridDim.x * blockDim.x) {
         const int i = me % fd.nx, j = me / fd.nx;
         if (box_frozen(fb, box, fd, i, j)) continue;
-        double nb[12];
+        const T tme = abs_(tf[me]);
+        if (!(tme < alf_inf<T>())) continue;
+        double t[12];
+        unsigned known = 0u;
         for (int k = 0; k < 12; ++k) {
             const int ii = i + kSlotDi[k], jj = j + kSlotDj[k];
-            if (ii < 0 || jj < 0 || ii >= fd.nx || jj >= fd.ny) {
-                nb[k] = alf_inf<double>();
-            } else {
-                const double v = fabs((double)tf[(long long)jj * fd.nx + ii]);
-                nb[k] = box_frozen(fb, box, fd, ii, jj) ? -v : v;
-            }
+            t[k] = alf_inf<double>();
+            if (ii < 0 || jj < 0 || ii >= fd.nx || jj >= fd.ny) continue;
+            const T v = abs_(tf[(long long)jj * fd.nx + ii]);
+            t[k] = (double)v;
+            const bool before = v < tme || (v == tme && ((kSlotDj[k] < 0) || (kSlotDj[k] == 0 && kSlotDi[k] < 0)));
+            if (box_frozen(fb, box, fd, ii, jj) || before) known |= 1u << k;
         }
         const RegionP<double> R = regions[(size_t)fd.sample * nregions + region_map[fd.map_off + me]];
-        int rec;
-        const double F = local_F<double>(nb, me, fd.nx, R, rec);
-        const double t = fabs((double)tf[me]);
-        if (t > 0.0 && t < alf_inf<double>()) mx = fmax(mx, fabs(F - t) / t);
+        double metric[16];
+        unsigned usable = 0u;
+        for (int p = 0; p < 16; ++p) {
+            const int A = kPairA[p], P = kPairP[p], Q = kPairQ[p];
+            metric[p] = alf_inf<double>();
+            if (((known >> A) & (known >> P) & (known >> Q) & 1u) == 0u) continue;
+            if (!(t[A] < t[P] && t[A] < t[Q])) continue;
+            const bool m1 = t[P] <= t[Q];
+            const double tB = m1 ? t[P] : t[Q], tC = m1 ? t[Q] : t[P];
+            metric[p] = (p < 8) ? (tC - tB)
+                                : fabs(t[Q] - ((1.4142135623730951 - 1.0) * t[A] + (2.0 - 1.4142135623730951) * t[P]));
+            usable |= 1u << p;
+        }
+        double F = alf_inf<double>();
+        int rec = 255;
+        for (int cls = 0; cls < 2 && rec == 255; ++cls) {
+            unsigned cand = usable & (cls == 0 ? 0x00FFu : 0xFF00u);
+            while (cand) {
+                int bp = -1;
+                for (unsigned m = cand; m; m &= m - 1) {
+                    const int p = __ffs(m) - 1;
+                    if (bp < 0 || metric[p] < metric[bp]) bp = p;
+                }
+                cand &= ~(1u << bp);
+                const int A = kPairA[bp], P = kPairP[bp], Q = kPairQ[bp];
+                const bool m1 = t[P] <= t[Q];
+                const int B = m1 ? P : Q, Cs = m1 ? Q : P;
+                const double v = stencil_time<double>(kSlotDi[A], kSlotDj[A], kSlotDi[B], kSlotDj[B], kSlotDi[Cs],
+                                                      kSlotDj[Cs], t[A], t[B], t[Cs], R);
+                if (v > t[Cs]) {
+                    F = v;
+                    rec = 2 * bp + (m1 ? 0 : 1);
+                    break;
+                }
+            }
+        }
+        if (rec == 255) {
+            for (int k = 0; k < 12; ++k) {
+                if (!((known >> k) & 1u)) continue;
+                const double g = t[k] + ((k >= 8) ? 2.0 * R.fb[kSlotClass[k]] : R.fb[kSlotClass[k]]);
+                if (g < F) {
+                    F = g;
+                    rec = 32 + k;
+                }
+            }
+        }
+        const double tt = (double)tme;
+        if (tt > 0.0) mx = fmax(mx, fabs(F - tt) / tt);
         if (records && records[fd.node_off + me] != (uint8_t)rec) flips++;
     }
     s_max[threadIdx.x] = mx;
@@ -587,6 +659,7 @@ cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fi
         check64_kernel<float><<<grid, 256, 0, st>>>((const float*)times, fields, region_map,
                                                     (const RegionP<double>*)regions64, nregions, records,
                                                     frozen_bits, box, max_rel, n_flips);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -250,6 +250,7 @@ cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st)
     const long long gs = (nrays + bs - 1) / bs;
     if (precision == ALF_FP64) ray_kernel<double><<<(unsigned)gs, bs, 0, st>>>(a);
     else ray_kernel<float><<<(unsigned)gs, bs, 0, st>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 
