@@ -258,7 +258,8 @@ def main():
 
     # ---- roofline of the dominant kernel (the evaluation of the local operator): its launches timed with
     # CUDA events on the solve's stream, over a second run of the same solves
-    Pt = api.Plan(wl, precision="fp32", device=local, time_kernels=1, band_cells=P.options.band_cells)
+    Pt = api.Plan(wl, precision="fp32", device=local, time_kernels=1, band_cells=P.options.band_cells,
+                  sweep=P.options.sweep)
     tt = Pt.new_times()
     Pt.solve(th, times=tt)
     ev_ms, evals, eval_launches = 0.0, 0, 0
@@ -296,6 +297,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fields": P.nfields, "nodes_per_step": P.total_nodes,
                    "rays_per_step": P.nfields * P.nrec, "band_cells": P.options.band_cells,
+                   "sweep": "one warp per field" if P.options.sweep == 2 else "lockstep rounds over all fields",
                    "l2": "inputs larger than L2 (3.6 GB of fields), no flush"},
         "stage_ms": stage, "evaluations_per_node": evals_per_node,
         "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},
@@ -303,7 +305,8 @@ def main():
                 "h2d_bytes_per_step": int(th_host.numel() * th_host.element_size()),
                 "d2h_bytes_per_step": int(rt_host.numel() * rt_host.element_size()
                                           + g_host.numel() * g_host.element_size())},
-        "roofline": {"bound": "alu", "kernel": "fim_eval_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "fim_warp_kernel" if P.options.sweep == 2 else "fim_eval_kernel",
+                     "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {clock:.0f} MHz (sampled clock); "
                                     f"{OPS_PER_EVAL:.0f} FP32 ops per evaluation",

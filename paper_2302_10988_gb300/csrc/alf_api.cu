@@ -174,7 +174,7 @@ void alf_default_options(alf_options* o)
     o->stop_radius = 1.6;
     o->max_ray_points = 512;
     o->max_rounds = 64;
-    o->cta_threads = 0;
+    o->sweep = 0;
     o->ctas_per_sm = 0;
     o->keep_records = 0;
     o->band_cells = 4.0;
@@ -231,6 +231,7 @@ static void plan_free(alf_plan* p)
     if (p->chunk_graph) cudaGraphExecDestroy(p->chunk_graph);
     for (auto& e : p->ev) cudaEventDestroy(e);
     dfree(p->d_fields);
+    dfree(p->d_order);
     dfree(p->d_adj_w);
     dfree(p->d_lambda);
     dfree(p->d_gnode);
@@ -294,8 +295,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     } else {
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
     }
-    if (opt.cta_threads != 0 && opt.cta_threads != 128 && opt.cta_threads != 256 && opt.cta_threads != 512)
-        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 128, 256 or 512");
+    if (opt.sweep < 0 || opt.sweep > 2) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1 or 2");
     if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 64) return fail(ctx, ALF_ERR_INVALID_ARG, "ctas_per_sm out of range");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
@@ -397,7 +397,20 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         }
     p->field_off.push_back(node_off);
     p->total_nodes = node_off;
-    if (opt.cta_threads == 0) opt.cta_threads = 128;
+    // field-resident sweep: the dirty bitmap of the largest field must fit in shared memory per warp
+    p->warp_words = (unsigned)((p->max_field_nodes + 31) / 32);
+    p->warp_grid = 0;
+    if (p->max_field_nodes <= (size_t(1) << 18)) {
+        const int c = fim_warp_ctas_per_sm(opt.precision, p->warp_words);
+        p->warp_grid = c > 0 ? c * ctx->nsm : 0;
+    }
+    if (opt.sweep == 2 && p->warp_grid == 0) {
+        delete p;
+        return fail(ctx, ALF_ERR_UNSUPPORTED, "sweep = 2: a field of %zu nodes does not fit the field-resident sweep",
+                    p->max_field_nodes);
+    }
+    p->sweep_mode = opt.sweep != 0 ? opt.sweep
+                    : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 1;
     // launch shapes of the sweep: one warp per field for the per-field steps, a
     // persistent-sized grid for the flat evaluation and marking steps
     p->grid_fields = std::max(1, std::min((p->nfields + 7) / 8, ctx->nsm * 16));
@@ -423,6 +436,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         }                                                               \
     } while (0)
     ALLOC(p->d_fields, p->fields.size());
+    ALLOC(p->d_order, p->fields.size());
     ALLOC(p->d_list0, p->total_nodes);
     ALLOC(p->d_list1, p->total_nodes);
     ALLOC(p->d_elist, p->total_nodes);
@@ -487,6 +501,15 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     };
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = up(p->d_fields, p->fields.data(), p->fields.size() * sizeof(FieldDesc));
+    {
+        // largest fields first: the field-resident sweep hands them out in this order
+        std::vector<unsigned> order(p->fields.size());
+        for (size_t f = 0; f < order.size(); ++f) order[f] = (unsigned)f;
+        std::stable_sort(order.begin(), order.end(), [&](unsigned x, unsigned y) {
+            return (long long)p->fields[x].nx * p->fields[x].ny > (long long)p->fields[y].nx * p->fields[y].ny;
+        });
+        if (e == cudaSuccess) e = up(p->d_order, order.data(), order.size() * sizeof(unsigned));
+    }
     if (e == cudaSuccess) e = up(p->d_map, g->region_map, p->total_map * sizeof(uint16_t));
     if (e == cudaSuccess) e = up(p->d_bm_off, bm_off.data(), bm_off.size() * sizeof(size_t));
     if (e == cudaSuccess) e = up(p->d_region_mat, g->region_material, (size_t)p->R * sizeof(uint16_t));
@@ -526,6 +549,7 @@ alf_status alf_plan_options(const alf_plan* p, alf_options* out)
 {
     if (!p || !out) return ALF_ERR_INVALID_ARG;
     *out = p->opt;
+    out->sweep = p->sweep_mode;
     return ALF_OK;
 }
 
@@ -571,8 +595,26 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     a.band_cells = p->opt.band_cells;
     a.q = p->d_q;
     a.records = records;
-    ALF_CUDA(ctx, launch_fim_init(prec, a, p->grid_fields, st));
-    {
+    if (p->sweep_mode == 2) {
+        // field-resident sweep: the whole fixed-point iteration in one launch
+        const bool timing = p->opt.time_kernels != 0;
+        if (timing && p->ev.size() < 2) {
+            p->ev.resize(2);
+            for (auto& e : p->ev) ALF_CUDA(ctx, cudaEventCreate(&e));
+        }
+        if (timing) ALF_CUDA(ctx, cudaEventRecord(p->ev[0], st));
+        ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
+        if (timing) {
+            ALF_CUDA(ctx, cudaEventRecord(p->ev[1], st));
+            ALF_CUDA(ctx, cudaEventSynchronize(p->ev[1]));
+            float ms = 0.f;
+            ALF_CUDA(ctx, cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
+            p->eval_ms = ms;
+            p->eval_launches = 1;
+        }
+        p->sweep_rounds = 0;  // per-field counts: alf_plan_stats reads the largest
+    } else {
+        ALF_CUDA(ctx, launch_fim_init(prec, a, p->grid_fields, st));
         const alf_status rc = run_sweep(p, a, st);
         if (rc != ALF_OK) return rc;
     }
@@ -715,7 +757,7 @@ alf_status alf_plan_stats(alf_plan* p, void* stream, alf_stats* out)
     ALF_CUDA(ctx, cudaMemcpyAsync(p->h_q, p->d_q, sizeof(QueueState), cudaMemcpyDeviceToHost, st));
     ALF_CUDA(ctx, cudaStreamSynchronize(st));
     out->node_evaluations = p->h_q->visits;
-    out->rounds = p->sweep_rounds;
+    out->rounds = p->sweep_mode == 2 ? p->h_q->rounds : p->sweep_rounds;
     out->nodes = (uint64_t)p->total_nodes;
     out->eval_launches = p->eval_launches;
     out->eval_ms = p->eval_ms;
@@ -730,42 +772,55 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     if (!theta || !times) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_plan_autotune: null theta or times");
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);
-    const double bands[4] = {2.0, 3.0, 4.0, 6.0};
-    const int blocks[2] = {128, 256};
+    // candidates: (schedule, band, evaluation block); a schedule fixed by the options is kept
+    struct Cand {
+        int mode;
+        double band;
+        int block;
+    };
+    std::vector<Cand> cands;
+    const bool try1 = p->opt.sweep != 2, try2 = p->opt.sweep != 1 && p->warp_grid > 0;
+    if (try1)
+        for (double band : {2.0, 3.0, 4.0, 6.0})
+            for (int blk : {128, 256}) cands.push_back({1, band, blk});
+    if (try2)
+        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block});
     double best_ms = 1e30, best_band = p->opt.band_cells;
-    int best_block = p->eval_block;
+    int best_block = p->eval_block, best_mode = p->sweep_mode;
     cudaEvent_t e0, e1;
     ALF_CUDA(ctx, cudaEventCreate(&e0));
     ALF_CUDA(ctx, cudaEventCreate(&e1));
     const int keep_timing = p->opt.time_kernels;
     p->opt.time_kernels = 0;
-    for (double band : bands)
-        for (int blk : blocks) {
-            p->opt.band_cells = band;
-            p->eval_block = blk;
-            if (p->chunk_graph) {
-                cudaGraphExecDestroy(p->chunk_graph);
-                p->chunk_graph = nullptr;
-            }
-            alf_status rc = alf_solve(p, theta, times, nullptr, records, stream);  // graph capture run
-            if (rc != ALF_OK) return rc;
-            ALF_CUDA(ctx, cudaEventRecord(e0, st));
-            rc = alf_solve(p, theta, times, nullptr, records, stream);
-            if (rc != ALF_OK) return rc;
-            ALF_CUDA(ctx, cudaEventRecord(e1, st));
-            ALF_CUDA(ctx, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            ALF_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_band = band;
-                best_block = blk;
-            }
+    for (const Cand& c : cands) {
+        p->opt.band_cells = c.band;
+        p->eval_block = c.block;
+        p->sweep_mode = c.mode;
+        if (p->chunk_graph) {
+            cudaGraphExecDestroy(p->chunk_graph);
+            p->chunk_graph = nullptr;
         }
+        alf_status rc = alf_solve(p, theta, times, nullptr, records, stream);  // warm-up (graph capture)
+        if (rc != ALF_OK) return rc;
+        ALF_CUDA(ctx, cudaEventRecord(e0, st));
+        rc = alf_solve(p, theta, times, nullptr, records, stream);
+        if (rc != ALF_OK) return rc;
+        ALF_CUDA(ctx, cudaEventRecord(e1, st));
+        ALF_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ALF_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_band = c.band;
+            best_block = c.block;
+            best_mode = c.mode;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->opt.band_cells = best_band;
     p->eval_block = best_block;
+    p->sweep_mode = best_mode;
     p->opt.time_kernels = keep_timing;
     if (p->chunk_graph) {
         cudaGraphExecDestroy(p->chunk_graph);

@@ -181,20 +181,30 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         if (neg_bit(nb[k])) fz |= 1u << k;
         else if (nb[k] < inf) cd |= 1u << k;
     }
-    // rank of each candidate in key order (tau, then linear index = static slot order);
-    // frozen slots are known from the start (rank -1), unknown ones never (rank 64)
+    // rank of each candidate in key order (tau, then linear index = static slot order):
+    // the number of candidates with a smaller key.  Non-candidates compare as +inf and
+    // are then given rank -1 (frozen: known from the start) or 64 (unknown: never known).
+    // (The pair loop runs over the full 12 x 12 square so that it unrolls completely and
+    // the arrays stay in registers.)
+    T kt[12];
     int rk[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? 0 : (((fz >> k) & 1u) ? -1 : 64);
+    for (int k = 0; k < 12; ++k) {
+        kt[k] = ((cd >> k) & 1u) ? t[k] : inf;
+        rk[k] = 0;
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
-        for (int m = k + 1; m < 12; ++m) {
-            if (((cd >> k) & (cd >> m) & 1u) == 0u) continue;
-            const bool lt = t[k] < t[m] || (t[k] == t[m] && sord(k) < sord(m));
+        for (int m = 0; m < 12; ++m) {
+            if (m <= k) continue;
+            // key(k) < key(m); on equal times the static order decides
+            const bool lt = sord(k) < sord(m) ? kt[k] <= kt[m] : kt[k] < kt[m];
             rk[m] += lt ? 1 : 0;
             rk[k] += lt ? 0 : 1;
         }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? rk[k] : (((fz >> k) & 1u) ? -1 : 64);
     const int nc = __popc(cd);
     // pairs: metric (+inf when not usable) and time
     T pm[16], pv[16];

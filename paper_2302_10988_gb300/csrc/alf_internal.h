@@ -76,6 +76,11 @@ cudaError_t launch_fim_round(int precision, const FimLaunch& a, int parity, int 
 void note_launches(unsigned n);
 unsigned long long launches_so_far();
 cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long long* out, cudaStream_t st);
+// field-resident sweep: one warp per field, fields taken in the order `order`
+#define ALF_SWEEP_WARPS 4
+cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* order, unsigned words_per_warp,
+                            int grid, cudaStream_t st);
+int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp);  // 0: does not fit
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -188,6 +193,11 @@ struct alf_plan {
     unsigned long long* d_pending = nullptr;
     unsigned long long* h_pending = nullptr;  // pinned
     int rounds_per_check = 32;
+    // field-resident sweep (option sweep = 2, or chosen by sweep = 0)
+    int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field
+    unsigned warp_words = 0;        // dirty-bitmap words of the largest field
+    int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
+    unsigned* d_order = nullptr;    // fields by decreasing size
     int eval_block = 128;           // threads per CTA of the evaluation step (autotuned)
     // CUDA graph of one chunk of rounds, for the pointers it was captured with
     cudaGraphExec_t chunk_graph = nullptr;

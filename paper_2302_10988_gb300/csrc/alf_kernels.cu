@@ -6,6 +6,7 @@
 //  init_radius    frozen straight-ray times around each source (Sec. 4.4)
 //  fim_*          bulk-synchronous dirty-set sweep of the local operator F to its
 //                 fixed point, all fields of the batch in every round
+//  fim_warp       the same sweep with one warp per field, the whole solve in one launch
 //  finalize       clears the frozen marks and gathers receiver times
 //  check64        FP64 evaluation of F at every node of a solved field
 #include <atomic>
@@ -444,6 +445,244 @@ __global__ void fim_pending_kernel(FimLaunch a, int parity, unsigned long long* 
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < a.nfields; f += gridDim.x * blockDim.x) s += c[f];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Field-resident sweep: one warp owns one field from its first dirty set to
+// its fixed point.  Each round is the same sequence as the bulk-synchronous
+// steps above -- front time T over the dirty set, the nodes within the band
+// split off and evaluated, then the marking rule -- with warp barriers between
+// the steps instead of kernel boundaries, and the field's dirty bitmap in
+// shared memory.  Warps take fields from a queue ordered by decreasing size.
+// All reads and writes of a field's times come from the one warp that owns it,
+// so plain (L1-cached) loads see every update after the warp barrier.
+// ---------------------------------------------------------------------------
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) fim_warp_kernel(FimLaunch a, const unsigned* order, unsigned words_per_warp)
+{
+    extern __shared__ unsigned s_bm[];
+    constexpr unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    unsigned* const bm = s_bm + (size_t)(threadIdx.x >> 5) * words_per_warp;
+    const T inf = alf_inf<T>();
+    const RegionP<T>* regions = (const RegionP<T>*)a.regions;
+    for (;;) {
+        unsigned fi = 0u, err = 0u;
+        if (lane == 0) {
+            fi = atomicAdd(&a.q->head, 1u);
+            err = ld_volatile(&a.q->error);
+        }
+        fi = __shfl_sync(FULL, fi, 0);
+        err = __shfl_sync(FULL, err, 0);
+        if (fi >= (unsigned)a.nfields || err != 0u) return;
+        const unsigned f = __ldg(order + fi);
+        const FieldDesc fd = a.fields[f];
+        const int nx = fd.nx, ny = fd.ny;
+        const unsigned words = (unsigned)((nx * ny + 31) / 32);
+        T* const tf = (T*)a.times + fd.node_off;
+        T* const ov = (T*)a.oldv + fd.node_off;
+        T* const nv = (T*)a.newv + fd.node_off;
+        unsigned* const el = a.elist + fd.node_off;
+        unsigned* const list0 = a.list[0] + fd.node_off;
+        unsigned* const list1 = a.list[1] + fd.node_off;
+        const RegionP<T>* reg = regions + (size_t)fd.sample * a.nregions;
+        const uint16_t* map = a.region_map + fd.map_off;
+        uint8_t* const rec = a.records ? a.records + fd.node_off : nullptr;
+        for (unsigned w = lane; w < words; w += 32u) bm[w] = 0u;
+        __syncwarp();
+        // first dirty set: the non-frozen nodes of the ring around the frozen box
+        unsigned nact = 0u;
+        {
+            const int r = a.box + 2, w = 2 * r + 1;
+            for (int base = 0; base < w * w; base += 32) {
+                const int k = base + (int)lane;
+                bool take = false;
+                unsigned n = 0u;
+                if (k < w * w) {
+                    const int i = fd.si + k % w - r, j = fd.sj + k / w - r;
+                    if (i >= 0 && j >= 0 && i < nx && j < ny) {
+                        n = (unsigned)(j * nx + i);
+                        take = !neg_bit(tf[n]);
+                    }
+                }
+                const unsigned bal = __ballot_sync(FULL, take);
+                if (take) {
+                    list0[nact + __popc(bal & below)] = n;
+                    atomicOr(bm + (n >> 5), 1u << (n & 31u));
+                }
+                nact += __popc(bal);
+            }
+        }
+        __syncwarp();
+        const T band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
+        const unsigned max_rounds = a.max_rounds_per_node * (unsigned)(nx + ny);
+        unsigned rounds = 0u, par = 0u;
+        unsigned long long evals = 0ull;
+        while (nact != 0u) {
+            if (++rounds > max_rounds) {
+                if (lane == 0) set_error(a.q, ALF_ERR_NOT_CONVERGED);
+                break;
+            }
+            const unsigned* LA = par ? list1 : list0;
+            unsigned* LB = par ? list0 : list1;
+            // front time of the dirty set and the band limit
+            auto m = order_key(inf);
+            for (unsigned k = lane; k < nact; k += 32u) {
+                const auto v = order_key(tf[LA[k]]);
+                m = v < m ? v : m;
+            }
+            const T lim = from_key(warp_min(m), T(0)) + band;
+            // split: in-band (or still unknown) nodes are evaluated, the rest wait
+            unsigned ne = 0u, nc = 0u;
+            for (unsigned base = 0; base < nact; base += 32u) {
+                const unsigned k = base + lane;
+                const bool in = k < nact;
+                bool ev = false;
+                unsigned n = 0u;
+                if (in) {
+                    n = LA[k];
+                    const T t = tf[n];
+                    ev = t <= lim || !(t < inf);
+                }
+                const unsigned be = __ballot_sync(FULL, in && ev), bc = __ballot_sync(FULL, in && !ev);
+                if (in && ev) {
+                    el[ne + __popc(be & below)] = n;
+                    atomicAnd(bm + (n >> 5), ~(1u << (n & 31u)));
+                } else if (in) {
+                    LB[nc + __popc(bc & below)] = n;
+                }
+                ne += __popc(be);
+                nc += __popc(bc);
+            }
+            __syncwarp();
+            // evaluate F at the in-band nodes (times updated in place)
+            for (unsigned e = lane; e < ne; e += 32u) {
+                const unsigned n = el[e];
+                const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+                T nb[12];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                    nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
+                }
+                const T old = tf[n];
+                const RegionP<T> R = reg[__ldg(map + n)];
+                int rc;
+                const T v = local_F<T>(nb, (int)n, nx, R, rc);
+                if (rec) rec[n] = (uint8_t)rc;
+                if (!same_bits(v, old)) tf[n] = v;
+                ov[e] = old;
+                nv[e] = v;
+            }
+            evals += ne;
+            __syncwarp();
+            // marking: changed nodes wake their later known neighbours; in-band nodes seed
+            // their unknown neighbours; an out-of-band node with unknown neighbours waits
+            for (unsigned base = 0; base < ne; base += 32u) {
+                const unsigned e = base + lane;
+                bool changed = false, inband = false, act = false;
+                unsigned n = 0u;
+                int i = 0, j = 0;
+                T v = inf, lo = inf;
+                if (e < ne) {
+                    const T o = ov[e];
+                    v = nv[e];
+                    changed = !same_bits(o, v);
+                    inband = v <= lim;
+                    act = changed || inband;
+                    n = el[e];
+                    i = (int)(n % (unsigned)nx);
+                    j = (int)(n / (unsigned)nx);
+                    lo = v < o ? v : o;
+                }
+                bool seeds_later = false;
+#pragma unroll
+                for (int q = 0; q < 13; ++q) {
+                    bool push = false;
+                    unsigned mnode = n;
+                    if (act) {
+                        if (q < 12) {
+                            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                            if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
+                                mnode = (unsigned)(jj * nx + ii);
+                                const T tm = tf[mnode];
+                                if (!neg_bit(tm)) {
+                                    if (tm < inf) push = changed && lo <= tm;
+                                    else if (inband) push = true;
+                                    else seeds_later = true;
+                                }
+                            }
+                        } else {
+                            push = seeds_later && v < inf;
+                        }
+                        if (push) {
+                            const unsigned bit = 1u << (mnode & 31u);
+                            push = (atomicOr(bm + (mnode >> 5), bit) & bit) == 0u;
+                        }
+                    }
+                    const unsigned bp = __ballot_sync(FULL, push);
+                    if (push) LB[nc + __popc(bp & below)] = mnode;
+                    nc += __popc(bp);
+                }
+            }
+            __syncwarp();
+            nact = nc;
+            par ^= 1u;
+        }
+        if (lane == 0) {
+            a.rounds[f] = rounds;
+            atomicAdd(&a.q->visits, evals);
+            atomicMax(&a.q->rounds, (unsigned long long)rounds);
+        }
+        __syncwarp();
+    }
+}
+
+// dynamic shared memory of the field-resident sweep: one dirty bitmap per warp
+template <typename T>
+static cudaError_t fim_warp_smem(unsigned words_per_warp, size_t* smem)
+{
+    *smem = (size_t)ALF_SWEEP_WARPS * words_per_warp * sizeof(unsigned);
+    if (*smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fim_warp_kernel<T, ALF_SWEEP_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)*smem);
+}
+
+template <typename T>
+static cudaError_t fim_warp_t(const FimLaunch& a, const unsigned* order, unsigned words_per_warp, int grid,
+                              cudaStream_t st)
+{
+    size_t smem = 0;
+    cudaError_t e = fim_warp_smem<T>(words_per_warp, &smem);
+    if (e != cudaSuccess) return e;
+    fim_warp_kernel<T, ALF_SWEEP_WARPS><<<grid, ALF_SWEEP_WARPS * 32, smem, st>>>(a, order, words_per_warp);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* order, unsigned words_per_warp,
+                            int grid, cudaStream_t st)
+{
+    return precision == ALF_FP64 ? fim_warp_t<double>(a, order, words_per_warp, grid, st)
+                                 : fim_warp_t<float>(a, order, words_per_warp, grid, st);
+}
+
+template <typename T>
+static int fim_warp_occ(unsigned words_per_warp)
+{
+    size_t smem = 0;
+    if (fim_warp_smem<T>(words_per_warp, &smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_warp_kernel<T, ALF_SWEEP_WARPS>, ALF_SWEEP_WARPS * 32,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp)
+{
+    return precision == ALF_FP64 ? fim_warp_occ<double>(words_per_warp) : fim_warp_occ<float>(words_per_warp);
 }
 
 template <typename T>

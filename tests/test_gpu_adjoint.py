@@ -54,5 +54,7 @@ def test_autograd_function(api):
     rec = P.new_records()
     times, rt = P.solve(theta.detach(), records=rec)
     g2 = P.backward(theta.detach(), times, rec, 2.0 * (rt - t_obs))
-    assert torch.allclose(g, g2, rtol=1e-6, atol=0)
+    # the adjoint accumulates FP32 sensitivities with atomics, so the two runs agree to FP32 rounding
+    # of the largest terms, not bit for bit
+    assert torch.allclose(g, g2, rtol=0, atol=1e-5 * g2.abs().max().item())
     assert torch.isfinite(g).all() and g.abs().max() > 0

@@ -62,12 +62,13 @@ def test_homogeneous_ti_fp64(api, oracle, group):
     assert np.allclose(rt.cpu().numpy()[0, 0], tau[r[:, 1], r[:, 0]], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("sweep", [1, 2])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
-def test_weld_ragged_parity(api, oracle, precision, tol):
+def test_weld_ragged_parity(api, oracle, precision, tol, sweep):
     wl = W.weld_single(n=100, h=0.5e-3, rg=5, seed=12, nsrc=3, nrec=5)
     wl.samples[0].src[:] = [[0, 0], [57, 0], [99, 0]]
     for band in (2.0, 4.0, 0.0):
-        P, th, times, rt, rec = _solve(api, wl, precision, band_cells=band)
+        P, th, times, rt, rec = _solve(api, wl, precision, band_cells=band, sweep=sweep)
         flips = 0
         for s in range(3):
             tau, orec, fr, M = oracle_field(oracle, wl, 0, s)
@@ -80,14 +81,15 @@ def test_weld_ragged_parity(api, oracle, precision, tol):
         print(f"{precision} band={band}: record flips {flips}")
 
 
-def test_tiny_and_edge_grids(api, oracle):
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_tiny_and_edge_grids(api, oracle, sweep):
     for (nx, ny, si, sj) in [(2, 2, 0, 0), (3, 7, 2, 6), (33, 9, 32, 0), (65, 17, 0, 16), (40, 40, 20, 20)]:
         rm = np.zeros((ny, nx), np.uint16)
         rm[:, nx // 2:] = 1
         s = W.Sample(nx, ny, 1e-3, rm, np.array([0.0, 0.7]), np.array([[si, sj]], np.int32),
                      np.array([[nx - 1 - si, ny - 1 - sj]], np.int32))
         wl = W.Workload("tiny", [W.WELD_TI, W.PARENT_ISO], np.array([0, 1], np.uint16), [s])
-        P, th, times, rt, rec = _solve(api, wl, "fp64")
+        P, th, times, rt, rec = _solve(api, wl, "fp64", sweep=sweep)
         tau, orec, fr, M = oracle_field(oracle, wl, 0, 0)
         assert rel_err(P.field(times, 0).cpu().numpy(), tau).max() < 1e-6
         assert record_mismatch(P.field(rec, 0).cpu().numpy(), orec, fr) == 0
@@ -119,9 +121,10 @@ def test_weld_256_fp64_and_fp32(api, oracle):
     assert mr64.max().item() < 1e-12 and int(fl64.sum()) == 0
 
 
-def test_uneven_batch_fp32(api, oracle):
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_uneven_batch_fp32(api, oracle, sweep):
     wl = W.weld_batch(nsamples=5, nsrc=3, nrec=4, sizes=(64, 96, 128, 160))
-    P, th, times, rt, rec = _solve(api, wl, "fp32")
+    P, th, times, rt, rec = _solve(api, wl, "fp32", sweep=sweep)
     worst = 0.0
     for b in range(5):
         for s in range(3):
@@ -147,7 +150,7 @@ def test_host_validation_errors(api):
     assert e.value.code == 2
     wl = W.homogeneous_ti()
     with pytest.raises(B.AlfError) as e:
-        api.Plan(wl, precision="fp64", cta_threads=5)
+        api.Plan(wl, precision="fp64", sweep=5)
     assert e.value.code == 1
 
 
@@ -173,3 +176,17 @@ def test_graph_stream_and_timing(api, oracle):
     assert (t3 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
     opt = Pt.autotune(th)
     assert opt.band_cells in (2.0, 3.0, 4.0, 6.0)
+
+
+def test_sweep_schedules_agree(api, oracle):
+    """Both sweep schedules reach the unique fixed point of F: in FP64 their fields and records are identical
+    bit for bit, on a batch of uneven fields, and they match the oracle."""
+    wl = W.weld_batch(nsamples=6, nsrc=4, nrec=4, sizes=(32, 64, 96, 128))
+    P1, th, t1, _, rec1 = _solve(api, wl, "fp64", sweep=1)
+    P2, _, t2, _, rec2 = _solve(api, wl, "fp64", sweep=2)
+    assert torch.equal(t1, t2)
+    assert torch.equal(rec1, rec2)
+    for b, s in ((0, 0), (3, 2), (5, 3)):
+        tau, orec, fr, M = oracle_field(oracle, wl, b, s)
+        assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
+        assert record_mismatch(P2.field(rec2, b * 4 + s).cpu().numpy(), orec, fr) == 0
