@@ -53,6 +53,10 @@ def _args():
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: direct launches on the default stream, no autotune, one warm-up step and "
                          "one step, a short summary line (for ncu)")
+    ap.add_argument("--profile-stages", default="all", choices=["all", "solve"],
+                    help="profiling run: the whole step, or the travel-time solve alone")
+    ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2],
+                    help="profiling run: sweep schedule (0: the library's choice)")
     return ap.parse_args()
 
 
@@ -161,17 +165,22 @@ def run_reference(args):
 def profile_run(args, wl, api, local):
     """One warm-up step and one step of the hot path with direct launches (no CUDA graph) on the default stream."""
     import torch
-    P = api.Plan(wl, precision="fp32", device=local, keep_records=1, use_graph=0, band_cells=2.0)
+    full = args.profile_stages == "all"
+    P = api.Plan(wl, precision="fp32", device=local, keep_records=int(full), use_graph=0, band_cells=2.0,
+                 sweep=args.sweep)
     th = P.theta_tensor()
-    times, rect, rec = P.new_times(), P.new_rec_times(), P.new_records()
+    times, rect = P.new_times(), P.new_rec_times()
+    rec = P.new_records() if full else None
     t0 = time.perf_counter()
     for _ in range(2):
         P.solve(th, times=times, rec_times=rect, records=rec)
-        P.check64(th, times, rec)
-        P.trace_rays(th, times)
-        P.backward(th, times, rec, 2.0 * rect)
+        if full:
+            P.check64(th, times, rec)
+            P.trace_rays(th, times)
+            P.backward(th, times, rec, 2.0 * rect)
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": True, "fields": P.nfields, "nodes": P.total_nodes, "status": P.status(),
+                      "sweep": P.options.sweep, "stages": args.profile_stages,
                       "seconds": time.perf_counter() - t0}), flush=True)
 
 

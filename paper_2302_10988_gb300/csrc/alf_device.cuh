@@ -87,7 +87,13 @@ ALF_D bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as
 ALF_D bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
 ALF_D float abs_(float v) { return fabsf(v); }
 ALF_D double abs_(double v) { return fabs(v); }
-ALF_D float sqrt_(float v) { return sqrtf(v); }
+// FP32: the hardware square-root approximation (relative error ~2^-23), well inside the FP32 path's budget
+ALF_D float sqrt_(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 ALF_D double sqrt_(double v) { return sqrt(v); }
 
 // ---------------------------------------------------------------------------
@@ -163,9 +169,15 @@ ALF_HD constexpr int pq(int p) { constexpr int t[16] = {0, 0, 3, 2, 6, 6, 4, 5, 
 // later than its later support point.
 //
 // Implementation: the 16 pair metrics and times do not depend on the known
-// set, so they are computed once; the walk over the known sets is a loop over
-// thresholds (the sorted neighbour keys), each step a handful of predicated
-// min-reductions.  The warp leaves the loop when all its lanes have stopped.
+// set, so they are computed once.  A pair becomes available at the step of its
+// latest member (rp = the largest rank of A, P, Q) and the fallback of slot q
+// at the step of q.  Within a class the choice is a minimum over a growing
+// set, so U changes only at steps where an item of the class in force (or of
+// a preferred class) becomes available.  With c(u) = the number of candidates
+// whose key precedes (u, me), the stop rule "(u_k, me) precedes the key of
+// rank k + 1" reads c(u_k) <= k + 1, and while U stays at u the first step
+// that satisfies it is c(u) - 1.  So the walk visits only the steps where U
+// can change and stops as soon as c(u) - 1 comes before the next of them.
 // ---------------------------------------------------------------------------
 template <typename T>
 ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
@@ -206,9 +218,10 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
 #pragma unroll
     for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? rk[k] : (((fz >> k) & 1u) ? -1 : 64);
     const int nc = __popc(cd);
-    // pairs: metric (+inf when not usable) and time
+    // pairs: metric (+inf when not usable), time, availability step; ev_*: bit (step + 1)
     T pm[16], pv[16];
-    unsigned prow_m2 = 0u;  // bit p: member 2 (tau_P > tau_Q)
+    int rp[16];
+    unsigned prow_m2 = 0u, ev_sq = 0u, ev_tr = 0u;  // prow_m2 bit p: member 2 (tau_P > tau_Q)
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         constexpr T k1 = T(1.4142135623730951) - T(1.0);
@@ -217,9 +230,10 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         const T tA = t[A], tP = t[P], tQ = t[Q];
         const bool m1 = tP <= tQ;
         if (!m1) prow_m2 |= 1u << p;
+        rp[p] = max(rk[A], max(rk[P], rk[Q]));
         pm[p] = inf;
         pv[p] = inf;
-        if (max(rk[A], max(rk[P], rk[Q])) < 64 && tA < tP && tA < tQ) {
+        if (rp[p] < 64 && tA < tP && tA < tQ) {
             const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
             const int xB = m1 ? sdi(P) : sdi(Q), yB = m1 ? sdj(P) : sdj(Q);
             const int xC = m1 ? sdi(Q) : sdi(P), yC = m1 ? sdj(Q) : sdj(P);
@@ -227,66 +241,63 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
             if (v > tC) {
                 pv[p] = v;
                 pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));
+                if (p < 8) ev_sq |= 1u << (rp[p] + 1);
+                else ev_tr |= 1u << (rp[p] + 1);
             }
         }
     }
-    // walk the prefixes: at step k the known set is the frozen slots and the candidates of rank <= k
+    // straight-ray fallback values of the slots
+    T g[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) g[q] = t[q] + ((q >= 8) ? T(2) * R.fb[scls(q)] : R.fb[scls(q)]);
+    const unsigned ev_all = ((1u << nc) - 1u) << 1;  // every candidate's step
+    // walk over the steps at which U can change; the known set at step k is the frozen slots
+    // and the candidates of rank <= k
     T u = inf;
     int urec = 255;
-    bool done = false;
+    int k = -1;
 #pragma unroll 1
-    for (int k = -1; k < 12; ++k) {
-        if (!done) {
-            unsigned known = 0u;
+    for (int guard = 0; guard < 14; ++guard) {
+        T bm = inf, bv = inf;
+        int br = 255, cls = 0;
 #pragma unroll
-            for (int q = 0; q < 12; ++q) known |= (rk[q] <= k ? 1u : 0u) << q;
-            T bm = inf, bv = inf;
-            int br = 255;
+        for (int p = 0; p < 8; ++p)
+            if (rp[p] <= k && pm[p] < bm) {
+                bm = pm[p];
+                bv = pv[p];
+                br = 2 * p + ((prow_m2 >> p) & 1u);
+            }
+        if (br == 255) {
+            cls = 1;
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
-                if (((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && pm[p] < bm) {
+            for (int p = 8; p < 16; ++p)
+                if (rp[p] <= k && pm[p] < bm) {
                     bm = pm[p];
                     bv = pv[p];
                     br = 2 * p + ((prow_m2 >> p) & 1u);
                 }
-            if (br == 255) {
-#pragma unroll
-                for (int p = 8; p < 16; ++p)
-                    if (((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && pm[p] < bm) {
-                        bm = pm[p];
-                        bv = pv[p];
-                        br = 2 * p + ((prow_m2 >> p) & 1u);
-                    }
-            }
-            if (br == 255) {
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    if (!((known >> q) & 1u)) continue;
-                    const T gq = t[q] + ((q >= 8) ? T(2) * R.fb[scls(q)] : R.fb[scls(q)]);
-                    if (gq < bv) {
-                        bv = gq;
-                        br = 32 + q;
-                    }
-                }
-            }
-            u = bv;
-            urec = br;
-            if (k + 1 >= nc) {
-                done = true;
-            } else {
-                // the neighbour of rank k + 1; stop when D's key (u, me) precedes it
-                T nt = inf;
-                int no = 0;
-#pragma unroll
-                for (int q = 0; q < 12; ++q)
-                    if (rk[q] == k + 1) {
-                        nt = t[q];
-                        no = sord(q);
-                    }
-                if (u < nt || (u == nt && 12 < no)) done = true;
-            }
         }
-        if (__all_sync(__activemask(), done)) break;
+        if (br == 255) {
+            cls = 2;
+#pragma unroll
+            for (int q = 0; q < 12; ++q)
+                if (rk[q] <= k && g[q] < bv) {
+                    bv = g[q];
+                    br = 32 + q;
+                }
+        }
+        u = bv;
+        urec = br;
+        // c(u): candidates whose key (tau, linear index) precedes (u, me)
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) cnt += (((cd >> q) & 1u) && (sord(q) < 12 ? t[q] <= u : t[q] < u)) ? 1 : 0;
+        if (cnt <= k + 1) break;
+        const unsigned later = (cls == 0 ? ev_sq : cls == 1 ? (ev_sq | ev_tr) : ev_all) >> (k + 2);
+        if (later == 0u) break;
+        const int e = k + __ffs((int)later);  // next step at which U can change
+        if (cnt - 1 < e) break;
+        k = e;
     }
     rec = urec;
     return u;

@@ -175,7 +175,7 @@ def test_graph_stream_and_timing(api, oracle):
     assert st["eval_launches"] > 0 and st["eval_ms"] > 0 and st["kernel_launches"] > 0
     assert (t3 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
     opt = Pt.autotune(th)
-    assert opt.band_cells in (2.0, 3.0, 4.0, 6.0)
+    assert opt.band_cells in (1.0, 2.0, 3.0, 4.0, 6.0) and opt.sweep in (1, 2)
 
 
 def test_sweep_schedules_agree(api, oracle):
