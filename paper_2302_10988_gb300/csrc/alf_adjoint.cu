@@ -13,9 +13,11 @@
 //             fallback and the frozen nodes) and the in-degree of every
 //             node (how many later nodes use it);
 //   seed      lambda = dL/dT at the receivers;
-//   rounds    Kahn's order, all fields at once: a node whose users have all
-//             been processed is final; it adds lambda * weight to the nodes
-//             it used and releases them (in-degree to zero -> next frontier);
+//   rounds    Kahn's order: a node whose users have all been processed is
+//             final; it adds lambda * weight to the nodes it used and releases
+//             them (in-degree to zero -> next frontier).  Either all fields
+//             advance in lockstep rounds (a few launches per round), or one
+//             warp owns each field and runs all its rounds in one launch;
 //   reduce    dL/dtheta_region = sum over the region's nodes of
 //             lambda * d(time)/d(theta) (frozen nodes: the source's region).
 // Every node is processed exactly once, so the sweep is exact and its work is
@@ -268,6 +270,94 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
     }
 }
 
+// first frontier of every field, one thread per node (field-resident schedule)
+__global__ void adj_frontier_flat_kernel(AdjLaunch a)
+{
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total_nodes;
+         g += (size_t)gridDim.x * blockDim.x) {
+        if (a.indeg[g] != 0u) continue;
+        int lo = 0, hi = a.nfields;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if ((size_t)a.fields[mid].node_off <= g) lo = mid; else hi = mid;
+        }
+        const size_t off = (size_t)a.fields[lo].node_off;
+        a.list[0][off + atomicAdd(a.cnt + lo, 1u)] = (unsigned)(g - off);
+    }
+}
+
+// Kahn rounds of one field by one warp, fields taken from a queue (largest first).  Only the owning
+// warp touches a field's lambda and in-degrees, and the warp barrier at the end of a round orders a
+// round's contributions before the next round reads them (through L2: __ldcg).
+template <typename T>
+__global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    T* const lam = (T*)a.lambda;
+    const AdjW<T>* W = (const AdjW<T>*)a.weights;
+    T* const gnode = (T*)a.gnode;
+    for (;;) {
+        unsigned fi = 0u;
+        if (lane == 0) fi = atomicAdd(a.head, 1u);
+        fi = __shfl_sync(FULL, fi, 0);
+        if (fi >= (unsigned)a.nfields) return;
+        const unsigned f = __ldg(a.order + fi);
+        const FieldDesc fd = a.fields[f];
+        const int nx = fd.nx, ny = fd.ny;
+        const size_t off = (size_t)fd.node_off;
+        const unsigned* fbits = a.frozen_bits + (size_t)f * frozen_words(a.box);
+        unsigned* const list0 = a.list[0] + off;
+        unsigned* const list1 = a.list[1] + off;
+        unsigned nact = a.cnt[f], par = 0u;
+        while (nact != 0u) {
+            const unsigned* LA = par ? list1 : list0;
+            unsigned* LB = par ? list0 : list1;
+            unsigned nc = 0u;
+            for (unsigned base = 0; base < nact; base += 32u) {
+                const unsigned e = base + lane;
+                unsigned m[3] = {0u, 0u, 0u};
+                bool fresh[3] = {false, false, false};
+                if (e < nact) {
+                    const unsigned n = LA[e];
+                    const size_t g = off + n;
+                    const T l = __ldcg(lam + g);
+                    const AdjW<T> w = W[g];
+                    gnode[g] = l * w.wt;
+                    const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+                    if (!frozen_at(fbits, a.box, fd, i, j)) {
+                        int s[3];
+                        int ns = support_slots(a.records[g], s);
+                        for (int k = 0; k < ns; ++k) {
+                            const int ii = i + kSlotDi[s[k]], jj = j + kSlotDj[s[k]];
+                            if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) ns = 0;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            if (k < ns) {
+                                m[k] = (unsigned)((j + kSlotDj[s[k]]) * nx + i + kSlotDi[s[k]]);
+                                atomicAdd(lam + off + m[k], l * w.w[k]);
+                            }
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            if (k < ns) fresh[k] = atomicSub(a.indeg + off + m[k], 1u) == 1u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const unsigned b = __ballot_sync(FULL, fresh[k]);
+                    if (fresh[k]) LB[nc + __popc(b & below)] = m[k];
+                    nc += __popc(b);
+                }
+            }
+            __syncwarp();
+            nact = nc;
+            par ^= 1u;
+        }
+    }
+}
+
 // dL/dtheta: per field, the node contributions summed by region (frozen nodes: the source's region)
 template <typename T>
 __global__ void adj_reduce_kernel(AdjLaunch a, double* grad)
@@ -318,6 +408,17 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
     if ((e = cudaMemsetAsync(grad, 0, (size_t)a.nsamples * a.nregions * sizeof(double), st)) != cudaSuccess) return e;
     adj_weights_kernel<T><<<grid, 256, 0, st>>>(a);
     adj_seed_kernel<T><<<64, 256, 0, st>>>(a, (const T*)dL_drec);
+    if (a.warp_grid > 0) {
+        // field-resident schedule: flat frontier, then every field's rounds in one launch
+        if ((e = cudaMemsetAsync(a.cnt, 0, (size_t)a.nfields * sizeof(unsigned), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(a.head, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+        adj_frontier_flat_kernel<<<grid, 256, 0, st>>>(a);
+        adj_warp_kernel<T><<<a.warp_grid, 256, 0, st>>>(a);
+        const size_t smem = a.nregions <= 4096 ? (size_t)a.nregions * sizeof(double) : 0;
+        adj_reduce_kernel<T><<<a.nfields, 256, smem, st>>>(a, grad);
+        note_launches(5);
+        return cudaGetLastError();
+    }
     adj_frontier_kernel<<<std::max(1, std::min((a.nfields + 7) / 8, grid)), 256, 0, st>>>(a);
     note_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

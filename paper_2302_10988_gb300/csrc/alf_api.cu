@@ -232,6 +232,7 @@ static void plan_free(alf_plan* p)
     for (auto& e : p->ev) cudaEventDestroy(e);
     dfree(p->d_fields);
     dfree(p->d_order);
+    dfree(p->d_adj_head);
     dfree(p->d_adj_w);
     dfree(p->d_lambda);
     dfree(p->d_gnode);
@@ -437,6 +438,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     } while (0)
     ALLOC(p->d_fields, p->fields.size());
     ALLOC(p->d_order, p->fields.size());
+    ALLOC(p->d_adj_head, 1);
     ALLOC(p->d_list0, p->total_nodes);
     ALLOC(p->d_list1, p->total_nodes);
     ALLOC(p->d_elist, p->total_nodes);
@@ -722,6 +724,9 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
     long long mx = 0;
     for (const FieldDesc& fd : p->fields) mx = std::max(mx, (long long)fd.nx * fd.ny);
     a.max_rounds = (unsigned)std::min<long long>(mx + 64, 0x7fffffffll);
+    a.order = p->d_order;
+    a.head = p->d_adj_head;
+    a.warp_grid = p->sweep_mode == 2 ? p->ctx->nsm * 8 : 0;  // 8 CTAs of 8 warps per SM
     ALF_CUDA(ctx, launch_adjoint(prec, a, dL_drec, dL_dtheta, p->d_pending, p->h_pending, p->grid_eval, st));
     return ALF_OK;
 }

@@ -116,6 +116,11 @@ struct AdjLaunch {
     unsigned* cnt;    // [2][nfields]
     unsigned* eoff;   // [nfields + 1]
     unsigned max_rounds;
+    // field-resident schedule (one warp per field, one launch): fields by decreasing size, a work
+    // counter, and the number of warps to launch (0: lockstep rounds over all fields instead)
+    const unsigned* order;
+    unsigned* head;
+    int warp_grid;
 };
 cudaError_t launch_adjoint(int precision, const AdjLaunch& a, const void* dL_drec, double* grad,
                            unsigned long long* d_pending, unsigned long long* h_pending, int grid, cudaStream_t st);
@@ -198,6 +203,7 @@ struct alf_plan {
     unsigned warp_words = 0;        // dirty-bitmap words of the largest field
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size
+    unsigned* d_adj_head = nullptr; // work counter of the field-resident adjoint
     int eval_block = 128;           // threads per CTA of the evaluation step (autotuned)
     // CUDA graph of one chunk of rounds, for the pointers it was captured with
     cudaGraphExec_t chunk_graph = nullptr;

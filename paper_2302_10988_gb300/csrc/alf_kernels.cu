@@ -778,11 +778,40 @@ ALF_D bool box_frozen(const unsigned* bits, int box, const FieldDesc& fd, int i,
 }
 
 // At a fixed point, F at D reads exactly the neighbours that precede D in key
-// order, so the check evaluates in FP64 the update U of that known set: pair
-// metrics and feasibility for all 16 pairs, then the time of the best usable
-// pair only (lazily: the next best when a pair is not usable), else the
-// fallback.  The FP64 work per node is a few dozen operations plus one or two
-// stencil times.
+// order, so the check evaluates in FP64 the update U of that known set.  The
+// FP64 pipe is the bottleneck, so only what needs it runs there: feasibility
+// and the square metrics tau_C - tau_B are exact on the stored times (a
+// difference of two FP32 times within a factor two of each other is exact in
+// FP32; a node with any other feasible square takes the all-FP64 path), the
+// best square is found by exact comparisons, and only its stencil time (the
+// next best's when it is not usable) is evaluated in FP64.  Triangle metrics
+// and the fallback, which need FP64 arithmetic, are evaluated only when no
+// square is usable.  All decisions are the ones an all-FP64 evaluation makes.
+template <typename T>
+ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R, int& rec)
+{
+    int xA = 0, yA = 0, xB = 0, yB = 0, xC = 0, yC = 0, r = 255;
+    T tA = T(0), tB = T(0), tC = T(0);
+#pragma unroll
+    for (int p = 0; p < 16; ++p)
+        if (p == bp) {
+            const bool m1 = t[pp(p)] <= t[pq(p)];
+            xA = sdi(pa(p));
+            yA = sdj(pa(p));
+            xB = m1 ? sdi(pp(p)) : sdi(pq(p));
+            yB = m1 ? sdj(pp(p)) : sdj(pq(p));
+            xC = m1 ? sdi(pq(p)) : sdi(pp(p));
+            yC = m1 ? sdj(pq(p)) : sdj(pp(p));
+            tA = t[pa(p)];
+            tB = m1 ? t[pp(p)] : t[pq(p)];
+            tC = m1 ? t[pq(p)] : t[pp(p)];
+            r = 2 * p + (m1 ? 0 : 1);
+        }
+    const double v = stencil_time<double>(xA, yA, xB, yB, xC, yC, (double)tA, (double)tB, (double)tC, R);
+    rec = r;
+    return v > (double)tC ? v : alf_inf<double>();
+}
+
 template <typename T>
 __global__ void check64_kernel(const T* times, const FieldDesc* fields, const uint16_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
@@ -792,76 +821,118 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, const ui
     const FieldDesc fd = fields[f];
     const unsigned* fb = frozen_bits + (size_t)f * frozen_words(box);
     const int n = fd.nx * fd.ny;
-    __shared__ double s_max[256];
+    __shared__ float s_max[256];
     __shared__ int s_flip[256];
-    double mx = 0.0;
+    float mx = 0.f;
     int flips = 0;
     const T* tf = times + fd.node_off;
+    const double inf64 = alf_inf<double>();
     for (int me = blockIdx.x * blockDim.x + threadIdx.x; me < n; me += gridDim.x * blockDim.x) {
         const int i = me % fd.nx, j = me / fd.nx;
         if (box_frozen(fb, box, fd, i, j)) continue;
         const T tme = abs_(tf[me]);
         if (!(tme < alf_inf<T>())) continue;
-        double t[12];
+        T t[12];
         unsigned known = 0u;
+#pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const int ii = i + kSlotDi[k], jj = j + kSlotDj[k];
-            t[k] = alf_inf<double>();
+            const int ii = i + sdi(k), jj = j + sdj(k);
+            t[k] = alf_inf<T>();
             if (ii < 0 || jj < 0 || ii >= fd.nx || jj >= fd.ny) continue;
             const T v = abs_(tf[(long long)jj * fd.nx + ii]);
-            t[k] = (double)v;
-            const bool before = v < tme || (v == tme && ((kSlotDj[k] < 0) || (kSlotDj[k] == 0 && kSlotDi[k] < 0)));
+            t[k] = v;
+            const bool before = sord(k) < 12 ? v <= tme : v < tme;
             if (box_frozen(fb, box, fd, ii, jj) || before) known |= 1u << k;
         }
         const RegionP<double> R = regions[(size_t)fd.sample * nregions + region_map[fd.map_off + me]];
-        double metric[16];
-        unsigned usable = 0u;
+        // feasible pairs (exact comparisons) and the square metrics
+        unsigned feas = 0u;
+        bool exact = true;
+        T msq[8];
+#pragma unroll
         for (int p = 0; p < 16; ++p) {
-            const int A = kPairA[p], P = kPairP[p], Q = kPairQ[p];
-            metric[p] = alf_inf<double>();
-            if (((known >> A) & (known >> P) & (known >> Q) & 1u) == 0u) continue;
-            if (!(t[A] < t[P] && t[A] < t[Q])) continue;
-            const bool m1 = t[P] <= t[Q];
-            const double tB = m1 ? t[P] : t[Q], tC = m1 ? t[Q] : t[P];
-            metric[p] = (p < 8) ? (tC - tB)
-                                : fabs(t[Q] - ((1.4142135623730951 - 1.0) * t[A] + (2.0 - 1.4142135623730951) * t[P]));
-            usable |= 1u << p;
+            const T tA = t[pa(p)], tP = t[pp(p)], tQ = t[pq(p)];
+            const bool ok = ((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && tA < tP && tA < tQ;
+            if (ok) feas |= 1u << p;
+            if (p < 8) {
+                const T lo = tP <= tQ ? tP : tQ, hi = tP <= tQ ? tQ : tP;
+                msq[p] = hi - lo;
+                if (ok && !(hi <= T(2) * lo)) exact = false;
+            }
         }
-        double F = alf_inf<double>();
+        double F = inf64;
         int rec = 255;
-        for (int cls = 0; cls < 2 && rec == 255; ++cls) {
-            unsigned cand = usable & (cls == 0 ? 0x00FFu : 0xFF00u);
-            while (cand) {
-                int bp = -1;
-                for (unsigned m = cand; m; m &= m - 1) {
-                    const int p = __ffs(m) - 1;
-                    if (bp < 0 || metric[p] < metric[bp]) bp = p;
+        // squares: best metric first, the next best when a pair is not usable
+        unsigned cand = feas & 0xFFu;
+#pragma unroll 1
+        for (int tries = 0; tries < 8 && cand; ++tries) {
+            int bp = -1;
+            if (exact) {
+                T bm = alf_inf<T>();
+#pragma unroll
+                for (int p = 0; p < 8; ++p)
+                    if (((cand >> p) & 1u) && (bp < 0 || msq[p] < bm)) {
+                        bm = msq[p];
+                        bp = p;
+                    }
+            } else {
+                double bm = inf64;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const double mp = fabs((double)t[pq(p)] - (double)t[pp(p)]);
+                    if (((cand >> p) & 1u) && (bp < 0 || mp < bm)) {
+                        bm = mp;
+                        bp = p;
+                    }
                 }
-                cand &= ~(1u << bp);
-                const int A = kPairA[bp], P = kPairP[bp], Q = kPairQ[bp];
-                const bool m1 = t[P] <= t[Q];
-                const int B = m1 ? P : Q, Cs = m1 ? Q : P;
-                const double v = stencil_time<double>(kSlotDi[A], kSlotDj[A], kSlotDi[B], kSlotDj[B], kSlotDi[Cs],
-                                                      kSlotDj[Cs], t[A], t[B], t[Cs], R);
-                if (v > t[Cs]) {
-                    F = v;
-                    rec = 2 * bp + (m1 ? 0 : 1);
-                    break;
+            }
+            cand &= ~(1u << bp);
+            int r;
+            const double v = check_pair_time<T>(bp, t, R, r);
+            if (v < inf64) {
+                F = v;
+                rec = r;
+                break;
+            }
+        }
+        // triangles (FP64 metrics), only when no square is usable
+        cand = rec == 255 ? (feas & 0xFF00u) : 0u;
+#pragma unroll 1
+        for (int tries = 0; tries < 8 && cand; ++tries) {
+            int bp = -1;
+            double bm = inf64;
+#pragma unroll
+            for (int p = 8; p < 16; ++p) {
+                const double mp = fabs((double)t[pq(p)] - ((1.4142135623730951 - 1.0) * (double)t[pa(p)] +
+                                                           (2.0 - 1.4142135623730951) * (double)t[pp(p)]));
+                if (((cand >> p) & 1u) && (bp < 0 || mp < bm)) {
+                    bm = mp;
+                    bp = p;
                 }
+            }
+            cand &= ~(1u << bp);
+            int r;
+            const double v = check_pair_time<T>(bp, t, R, r);
+            if (v < inf64) {
+                F = v;
+                rec = r;
+                break;
             }
         }
         if (rec == 255) {
+#pragma unroll
             for (int k = 0; k < 12; ++k) {
                 if (!((known >> k) & 1u)) continue;
-                const double g = t[k] + ((k >= 8) ? 2.0 * R.fb[kSlotClass[k]] : R.fb[kSlotClass[k]]);
+                const double g = (double)t[k] + ((k >= 8) ? 2.0 * R.fb[scls(k)] : R.fb[scls(k)]);
                 if (g < F) {
                     F = g;
                     rec = 32 + k;
                 }
             }
         }
-        const double tt = (double)tme;
-        if (tt > 0.0) mx = fmax(mx, fabs(F - tt) / tt);
+        // relative residual: the difference in FP64, its ratio in FP32
+        const float res = fabsf((float)(F - (double)tme)) / (float)tme;
+        if (tme > T(0)) mx = fmaxf(mx, res);
         if (records && records[fd.node_off + me] != (uint8_t)rec) flips++;
     }
     s_max[threadIdx.x] = mx;
@@ -869,14 +940,14 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, const ui
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
-            s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+            s_max[threadIdx.x] = fmaxf(s_max[threadIdx.x], s_max[threadIdx.x + o]);
             s_flip[threadIdx.x] += s_flip[threadIdx.x + o];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         // max of non-negative doubles through their bit patterns
-        atomicMax((unsigned long long*)(max_rel + f), (unsigned long long)__double_as_longlong(s_max[0]));
+        atomicMax((unsigned long long*)(max_rel + f), (unsigned long long)__double_as_longlong((double)s_max[0]));
         atomicAdd(n_flips + f, s_flip[0]);
     }
 }

@@ -21,12 +21,13 @@ def _problem(nsamples=3, n=56):
     return wl, truth
 
 
+@pytest.mark.parametrize("sweep", [1, 2])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 2e-3)])
-def test_backward_matches_oracle(api, oracle, precision, tol):
+def test_backward_matches_oracle(api, oracle, precision, tol, sweep):
     wl, truth = _problem()
     _, _, t_true = oracle.misfit_and_gradient(truth, 0, truth.samples[0].region_theta, np.zeros((3, 6)))
     t_obs = t_true + W.observation_noise(t_true.shape)
-    P = api.Plan(wl, precision=precision, keep_records=1)
+    P = api.Plan(wl, precision=precision, keep_records=1, sweep=sweep)
     th = P.theta_tensor()
     rec = P.new_records()
     times, rt = P.solve(th, records=rec)
@@ -58,3 +59,18 @@ def test_autograd_function(api):
     # of the largest terms, not bit for bit
     assert torch.allclose(g, g2, rtol=0, atol=1e-5 * g2.abs().max().item())
     assert torch.isfinite(g).all() and g.abs().max() > 0
+
+
+def test_adjoint_schedules_agree(api):
+    """The lockstep and field-resident adjoint sweeps give the same FP64 gradient (up to the order of the
+    atomic additions) on a batch of uneven fields."""
+    wl = W.weld_batch(nsamples=4, nsrc=3, nrec=5, sizes=(32, 64, 96))
+    out = []
+    for sweep in (1, 2):
+        P = api.Plan(wl, precision="fp64", keep_records=1, sweep=sweep)
+        th = P.theta_tensor()
+        rec = P.new_records()
+        times, rt = P.solve(th, records=rec)
+        out.append(P.backward(th, times, rec, 2.0 * rt))
+        assert P.status() == 0
+    assert torch.allclose(out[0], out[1], rtol=0, atol=1e-9 * out[0].abs().max().item())
