@@ -16,8 +16,9 @@ Inputs are synthetic and seeded; the packed fields (3.6 GB FP32) are larger
 than L2, so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-With N > 1 (launched by torchrun) every rank solves its own copy of the batch
-(weak scaling, no collective on the data path) and rank 0 prints the line.
+With N > 1 (launched by torchrun) every rank solves its own batch of the same shape
+(its own seeded orientation draws; weak scaling, no collective on the data path), the
+step time is the slowest rank's, and rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -103,6 +104,23 @@ class Clocks:
         reasons = sorted({n for r in ok for k, n in enumerate(names) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons}
+
+
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's step time (the whole job finishes when its last rank does)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(W, nsamples: int, rank: int):
+    """Rank `rank`'s own batch: same shape and size as rank 0's, its own orientation draws."""
+    return W.weld_batch(nsamples=nsamples, seed=W.rank_seed(2, rank))
 
 
 def _peaks():
@@ -199,7 +217,7 @@ def main():
     __graft_entry__.build()
     from paper_2302_10988_gb300 import api, workloads as W
 
-    wl = W.weld_batch(nsamples=args.samples)
+    wl = rank_workload(W, args.samples, rank)
     if args.profile:
         return profile_run(args, wl, api, local)
     stream = torch.cuda.Stream()
@@ -252,11 +270,7 @@ def main():
     torch.cuda.synchronize()
     ck = clocks.stop()
     launches = (P.stats()["kernel_launches"] - launches0) // args.steps
-    ms = start.elapsed_time(end) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end) / args.steps, world)
     if P.status() != 0:
         raise SystemExit("device status non-zero in the timed region")
     nodes = P.total_nodes * world

@@ -164,6 +164,11 @@ def weld_batch(nsamples=512, nsrc=32, nrec=32, sizes=tuple(range(128, 321, 32)),
                     samples)
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s own batch when several processes each solve a batch (weak scaling)."""
+    return int(seed) + 7919 * int(rank)
+
+
 def weld_adjoint(nsamples=256, n=200, h=0.5e-3, rg=10, nsrc=32, nrec=32, truth_seed=3, sample_seed=30):
     """Adjoint workload: truth orientations (seed 3) and nsamples candidate orientation sets (seed 30)."""
     mats, rmat = _weld_materials(rg)
