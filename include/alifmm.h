@@ -77,7 +77,13 @@ typedef enum { ALF_GROUP_PAPER = 0, ALF_GROUP_EXACT = 1 } alf_group_model;
  *                      around the source is homogeneous);
  *  ALF_INIT_HIERARCHY: the paper's refined grids (densities level_density[],
  *                      out to level_radius[] original cells), straight rays
- *                      inside the source cell on the finest one. */
+ *                      inside the source cell on the finest one; each level
+ *                      stops at the first node on the boundary of its square
+ *                      (in key order) and hands its known nodes that coincide
+ *                      with the next level's nodes to it as frozen nodes.
+ *                      Level grids are at most 2^16 nodes.  alf_backward does
+ *                      not differentiate this initialisation
+ *                      (ALF_ERR_UNSUPPORTED). */
 typedef enum { ALF_INIT_RADIUS = 0, ALF_INIT_HIERARCHY = 1 } alf_init_mode;
 
 /* One material: 6x6 Voigt stiffness (Pa) and density (kg/m^3).  Only the
@@ -215,7 +221,7 @@ alf_status alf_trace_rays(alf_plan* plan, const double* region_theta, const void
  * receiver, returns dL/dtheta for every region, by differentiating the chosen
  * stencil (or fallback) of every node and the straight-ray initialisation,
  * swept in reverse causal order.  Needs a plan created with keep_records = 1
- * and the times and records of the same solve.
+ * and init_mode = ALF_INIT_RADIUS, and the times and records of the same solve.
  *  dL_drec      [nsamples][nsources][nreceivers], dtype of the plan, input
  *  dL_dtheta    [nsamples][nregions] double, output (overwritten) */
 alf_status alf_backward(alf_plan* plan, const double* region_theta, const void* times, const uint8_t* records,

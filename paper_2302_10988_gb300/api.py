@@ -40,8 +40,9 @@ class Plan:
     """A batch of fields (samples x sources) of one workload, ready to solve.
 
     Keyword options map to ``alf_options`` fields (precision "fp32"/"fp64",
-    group "paper"/"exact", init_radius, plane_step, ray_halfwidth, stop_radius,
-    max_ray_points, max_rounds, keep_records, band_cells, use_graph, time_kernels)."""
+    group "paper"/"exact", init_mode, init_radius, n_levels, level_density, level_radius,
+    plane_step, ray_halfwidth, stop_radius, max_ray_points, max_rounds, sweep, keep_records,
+    band_cells, use_graph, time_kernels); array fields take a sequence of 4 ints."""
 
     def __init__(self, wl, precision="fp32", group="paper", device=0, **opts):
         self.wl = wl
@@ -54,6 +55,8 @@ class Plan:
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
+            if k in ("level_density", "level_radius"):
+                v = tuple(v) + (0,) * (4 - len(v))
             setattr(o, k, v)
         S = len(wl.samples[0].src)
         Rr = len(wl.samples[0].rec)

@@ -233,6 +233,8 @@ static void plan_free(alf_plan* p)
     dfree(p->d_fields);
     dfree(p->d_order);
     dfree(p->d_adj_head);
+    dfree(p->d_hier);
+    dfree(p->d_hier_head);
     dfree(p->d_adj_w);
     dfree(p->d_lambda);
     dfree(p->d_gnode);
@@ -292,7 +294,6 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
             if ((2 * r * d + 1) * (2 * r * d + 1) > (1 << 16))
                 return fail(ctx, ALF_ERR_INVALID_ARG, "level %d grid too large (%d^2 nodes)", l, 2 * r * d + 1);
         }
-        return fail(ctx, ALF_ERR_UNSUPPORTED, "ALF_INIT_HIERARCHY is not available in this build");
     } else {
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
     }
@@ -327,7 +328,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     p->R = g->nregions;
     p->nmat = g->nmaterials;
     p->nfields = p->B * p->S;
-    p->box = opt.init_radius;
+    p->box = opt.init_mode == ALF_INIT_HIERARCHY ? opt.level_radius[opt.n_levels - 1] : opt.init_radius;
     size_t map_off = 0, node_off = 0;
     std::vector<long long> map_offs(p->B);
     for (int b = 0; b < p->B; ++b) {
@@ -439,6 +440,22 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     ALLOC(p->d_fields, p->fields.size());
     ALLOC(p->d_order, p->fields.size());
     ALLOC(p->d_adj_head, 1);
+    if (opt.init_mode == ALF_INIT_HIERARCHY) {
+        size_t cap = 0;
+        for (int l = 0; l < opt.n_levels; ++l) {
+            const size_t side = 2 * (size_t)opt.level_radius[l] * opt.level_density[l] + 1;
+            cap = std::max(cap, side * side);
+        }
+        p->hier_cap = cap;
+        // one warp per field at a time; scratch bounded to about 2 GB
+        const size_t stride = hier_scratch_bytes(opt.precision, cap);
+        const size_t by_mem = std::max<size_t>(1, (size_t(2) << 30) / stride);
+        p->hier_warps = (int)std::min<size_t>({(size_t)p->nfields, (size_t)ctx->nsm * 16, by_mem});
+        char* hs = nullptr;
+        ALLOC(hs, (size_t)p->hier_warps * stride);
+        p->d_hier = hs;
+        ALLOC(p->d_hier_head, 1);
+    }
     ALLOC(p->d_list0, p->total_nodes);
     ALLOC(p->d_list1, p->total_nodes);
     ALLOC(p->d_elist, p->total_nodes);
@@ -569,9 +586,41 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     ALF_CUDA(ctx, launch_fill_inf(prec, times, p->total_nodes, st));
     if (records) ALF_CUDA(ctx, cudaMemsetAsync(records, 255, p->total_nodes, st));
     ALF_CUDA(ctx, cudaMemsetAsync(p->d_frozen, 0, sizeof(unsigned) * (size_t)p->nfields * frozen_words(p->box), st));
-    ALF_CUDA(ctx, launch_init_radius(prec, times, p->d_fields, p->nfields, p->d_map, p->d_region_mat, p->d_mats, theta,
-                                     p->d_h, p->R, p->opt.init_radius, gm, p->d_frozen, p->box, st));
     ALF_CUDA(ctx, cudaMemsetAsync(p->d_q, 0, sizeof(QueueState), st));
+    if (p->opt.init_mode == ALF_INIT_HIERARCHY) {
+        ALF_CUDA(ctx, cudaMemsetAsync(p->d_hier_head, 0, sizeof(unsigned), st));
+        HierLaunch h;
+        h.times = times;
+        h.fields = p->d_fields;
+        h.nfields = p->nfields;
+        h.region_map = p->d_map;
+        h.region_mat = p->d_region_mat;
+        h.mats = p->d_mats;
+        h.regions = p->d_regions;
+        h.theta = theta;
+        h.h = p->d_h;
+        h.nregions = p->R;
+        h.group_model = gm;
+        h.nlev = p->opt.n_levels;
+        for (int l = 0; l < 4; ++l) {
+            h.dens[l] = p->opt.level_density[l];
+            h.rad[l] = p->opt.level_radius[l];
+        }
+        h.box = p->box;
+        h.frozen_bits = p->d_frozen;
+        h.level_cap = p->hier_cap;
+        h.scratch = p->d_hier;
+        h.scratch_stride = hier_scratch_bytes(prec, p->hier_cap);
+        h.nwarps = p->hier_warps;
+        h.head = p->d_hier_head;
+        h.q = p->d_q;
+        h.band_cells = p->opt.band_cells;
+        h.max_rounds_per_node = (unsigned)p->opt.max_rounds;
+        ALF_CUDA(ctx, launch_init_hierarchy(prec, h, st));
+    } else {
+        ALF_CUDA(ctx, launch_init_radius(prec, times, p->d_fields, p->nfields, p->d_map, p->d_region_mat, p->d_mats,
+                                         theta, p->d_h, p->R, p->opt.init_radius, gm, p->d_frozen, p->box, st));
+    }
     FimLaunch a;
     a.times = times;
     a.fields = p->d_fields;
@@ -688,6 +737,8 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: null pointer");
     if (!p->opt.keep_records || !p->d_adj_w)
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: the plan was created without keep_records");
+    if (p->opt.init_mode != ALF_INIT_RADIUS)
+        return fail(ctx, ALF_ERR_UNSUPPORTED, "alf_backward: only the straight-ray initialisation is differentiated");
     if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: plan has no receivers");
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);

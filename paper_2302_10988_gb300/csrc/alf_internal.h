@@ -90,6 +90,36 @@ cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fi
 cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
                                  double* out, int n, cudaStream_t st);
 
+// near-source hierarchy (alf_hier.cu)
+struct HierLaunch {
+    void* times;
+    const FieldDesc* fields;
+    int nfields;
+    const uint16_t* region_map;
+    const uint16_t* region_mat;
+    const MatD* mats;
+    const void* regions;  // RegionP<T>
+    const double* theta;
+    const double* h;
+    int nregions;
+    int group_model;
+    int nlev;
+    int dens[4];
+    int rad[4];
+    int box;                 // = rad[nlev - 1]: half-width of the frozen box on the original grid
+    unsigned* frozen_bits;
+    size_t level_cap;        // nodes of the largest level grid
+    void* scratch;           // per warp: scratch_stride bytes
+    size_t scratch_stride;   // hier_scratch_bytes(precision, level_cap)
+    int nwarps;              // warps launched (one field at a time each)
+    unsigned* head;          // field counter
+    QueueState* q;           // error word
+    double band_cells;
+    unsigned max_rounds_per_node;
+};
+size_t hier_scratch_bytes(int precision, size_t level_cap);
+cudaError_t launch_init_hierarchy(int precision, const HierLaunch& a, cudaStream_t st);
+
 // adjoint (alf_adjoint.cu)
 struct AdjLaunch {
     const void* times;
@@ -204,6 +234,11 @@ struct alf_plan {
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size
     unsigned* d_adj_head = nullptr; // work counter of the field-resident adjoint
+    // near-source hierarchy (init_mode = ALF_INIT_HIERARCHY)
+    size_t hier_cap = 0;            // nodes of the largest level grid
+    int hier_warps = 0;
+    void* d_hier = nullptr;         // per-warp level scratch
+    unsigned* d_hier_head = nullptr;
     int eval_block = 128;           // threads per CTA of the evaluation step (autotuned)
     // CUDA graph of one chunk of rounds, for the pointers it was captured with
     cudaGraphExec_t chunk_graph = nullptr;

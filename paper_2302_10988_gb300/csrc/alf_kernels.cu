@@ -13,6 +13,7 @@
 #include <cstdio>
 
 #include "alf_internal.h"
+#include "alf_sweep.cuh"
 
 namespace alf {
 
@@ -197,20 +198,6 @@ cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fiel
 // The marking runs after all writes of the round, so it compares against
 // written times.  A field is at the fixed point of F when its dirty set is
 // empty.  Frozen nodes carry the sign bit and are never listed.
-ALF_D unsigned order_key(float v) { return __float_as_uint(v); }  // v >= 0
-ALF_D unsigned long long order_key(double v) { return (unsigned long long)__double_as_longlong(v); }
-ALF_D float from_key(unsigned k, float) { return __uint_as_float(k); }
-ALF_D double from_key(unsigned long long k, double) { return __longlong_as_double((long long)k); }
-ALF_D unsigned warp_min(unsigned v) { return __reduce_min_sync(0xffffffffu, v); }
-ALF_D unsigned long long warp_min(unsigned long long v)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w < v ? w : v;
-    }
-    return v;
-}
-
 // first dirty set of every field: the non-frozen nodes around the frozen box
 template <typename T>
 __global__ void fim_init_kernel(FimLaunch a)
@@ -455,18 +442,19 @@ __global__ void fim_pending_kernel(FimLaunch a, int parity, unsigned long long* 
 // the steps instead of kernel boundaries, and the field's dirty bitmap in
 // shared memory.  Warps take fields from a queue ordered by decreasing size.
 // All reads and writes of a field's times come from the one warp that owns it,
-// so plain (L1-cached) loads see every update after the warp barrier.
+// so plain (L1-cached) loads see every update after the warp barrier.  The
+// same routine sweeps the finer grids of the near-source hierarchy (spacing
+// h / d, `scale` = 1 / d).
 // ---------------------------------------------------------------------------
+// FP32: registers capped so that four 4-warp CTAs fit an SM (what the shared bitmaps of 320 x 320 fields allow)
 template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32) fim_warp_kernel(FimLaunch a, const unsigned* order, unsigned words_per_warp)
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
+    fim_warp_kernel(FimLaunch a, const unsigned* order, unsigned words_per_warp)
 {
     extern __shared__ unsigned s_bm[];
     constexpr unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned below = (1u << lane) - 1u;
-    unsigned* const bm = s_bm + (size_t)(threadIdx.x >> 5) * words_per_warp;
     const T inf = alf_inf<T>();
-    const RegionP<T>* regions = (const RegionP<T>*)a.regions;
     for (;;) {
         unsigned fi = 0u, err = 0u;
         if (lane == 0) {
@@ -478,159 +466,29 @@ __global__ void __launch_bounds__(NW * 32) fim_warp_kernel(FimLaunch a, const un
         if (fi >= (unsigned)a.nfields || err != 0u) return;
         const unsigned f = __ldg(order + fi);
         const FieldDesc fd = a.fields[f];
-        const int nx = fd.nx, ny = fd.ny;
-        const unsigned words = (unsigned)((nx * ny + 31) / 32);
-        T* const tf = (T*)a.times + fd.node_off;
-        T* const ov = (T*)a.oldv + fd.node_off;
-        T* const nv = (T*)a.newv + fd.node_off;
-        unsigned* const el = a.elist + fd.node_off;
-        unsigned* const list0 = a.list[0] + fd.node_off;
-        unsigned* const list1 = a.list[1] + fd.node_off;
-        const RegionP<T>* reg = regions + (size_t)fd.sample * a.nregions;
-        const uint16_t* map = a.region_map + fd.map_off;
-        uint8_t* const rec = a.records ? a.records + fd.node_off : nullptr;
-        for (unsigned w = lane; w < words; w += 32u) bm[w] = 0u;
-        __syncwarp();
-        // first dirty set: the non-frozen nodes of the ring around the frozen box
-        unsigned nact = 0u;
-        {
-            const int r = a.box + 2, w = 2 * r + 1;
-            for (int base = 0; base < w * w; base += 32) {
-                const int k = base + (int)lane;
-                bool take = false;
-                unsigned n = 0u;
-                if (k < w * w) {
-                    const int i = fd.si + k % w - r, j = fd.sj + k / w - r;
-                    if (i >= 0 && j >= 0 && i < nx && j < ny) {
-                        n = (unsigned)(j * nx + i);
-                        take = !neg_bit(tf[n]);
-                    }
-                }
-                const unsigned bal = __ballot_sync(FULL, take);
-                if (take) {
-                    list0[nact + __popc(bal & below)] = n;
-                    atomicOr(bm + (n >> 5), 1u << (n & 31u));
-                }
-                nact += __popc(bal);
-            }
-        }
-        __syncwarp();
-        const T band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
-        const unsigned max_rounds = a.max_rounds_per_node * (unsigned)(nx + ny);
-        unsigned rounds = 0u, par = 0u;
+        WarpGrid<T> g;
+        g.tf = (T*)a.times + fd.node_off;
+        g.nx = fd.nx;
+        g.ny = fd.ny;
+        g.map = a.region_map + fd.map_off;
+        g.reg = (const RegionP<T>*)a.regions + (size_t)fd.sample * a.nregions;
+        g.scale = T(1);
+        g.list0 = a.list[0] + fd.node_off;
+        g.list1 = a.list[1] + fd.node_off;
+        g.el = a.elist + fd.node_off;
+        g.ov = (T*)a.oldv + fd.node_off;
+        g.nv = (T*)a.newv + fd.node_off;
+        g.rec = a.records ? a.records + fd.node_off : nullptr;
+        g.bm = s_bm + (size_t)(threadIdx.x >> 5) * words_per_warp;
+        g.band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
+        g.max_rounds = a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny);
+        // first dirty set: the non-frozen nodes of the square around the frozen box
+        const unsigned nact = warp_seed_square(g, fd.si, fd.sj, a.box + 2);
         unsigned long long evals = 0ull;
-        while (nact != 0u) {
-            if (++rounds > max_rounds) {
-                if (lane == 0) set_error(a.q, ALF_ERR_NOT_CONVERGED);
-                break;
-            }
-            const unsigned* LA = par ? list1 : list0;
-            unsigned* LB = par ? list0 : list1;
-            // front time of the dirty set and the band limit
-            auto m = order_key(inf);
-            for (unsigned k = lane; k < nact; k += 32u) {
-                const auto v = order_key(tf[LA[k]]);
-                m = v < m ? v : m;
-            }
-            const T lim = from_key(warp_min(m), T(0)) + band;
-            // split: in-band (or still unknown) nodes are evaluated, the rest wait
-            unsigned ne = 0u, nc = 0u;
-            for (unsigned base = 0; base < nact; base += 32u) {
-                const unsigned k = base + lane;
-                const bool in = k < nact;
-                bool ev = false;
-                unsigned n = 0u;
-                if (in) {
-                    n = LA[k];
-                    const T t = tf[n];
-                    ev = t <= lim || !(t < inf);
-                }
-                const unsigned be = __ballot_sync(FULL, in && ev), bc = __ballot_sync(FULL, in && !ev);
-                if (in && ev) {
-                    el[ne + __popc(be & below)] = n;
-                    atomicAnd(bm + (n >> 5), ~(1u << (n & 31u)));
-                } else if (in) {
-                    LB[nc + __popc(bc & below)] = n;
-                }
-                ne += __popc(be);
-                nc += __popc(bc);
-            }
-            __syncwarp();
-            // evaluate F at the in-band nodes (times updated in place)
-            for (unsigned e = lane; e < ne; e += 32u) {
-                const unsigned n = el[e];
-                const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                T nb[12];
-#pragma unroll
-                for (int q = 0; q < 12; ++q) {
-                    const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
-                    nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
-                }
-                const T old = tf[n];
-                const RegionP<T> R = reg[__ldg(map + n)];
-                int rc;
-                const T v = local_F<T>(nb, (int)n, nx, R, rc);
-                if (rec) rec[n] = (uint8_t)rc;
-                if (!same_bits(v, old)) tf[n] = v;
-                ov[e] = old;
-                nv[e] = v;
-            }
-            evals += ne;
-            __syncwarp();
-            // marking: changed nodes wake their later known neighbours; in-band nodes seed
-            // their unknown neighbours; an out-of-band node with unknown neighbours waits
-            for (unsigned base = 0; base < ne; base += 32u) {
-                const unsigned e = base + lane;
-                bool changed = false, inband = false, act = false;
-                unsigned n = 0u;
-                int i = 0, j = 0;
-                T v = inf, lo = inf;
-                if (e < ne) {
-                    const T o = ov[e];
-                    v = nv[e];
-                    changed = !same_bits(o, v);
-                    inband = v <= lim;
-                    act = changed || inband;
-                    n = el[e];
-                    i = (int)(n % (unsigned)nx);
-                    j = (int)(n / (unsigned)nx);
-                    lo = v < o ? v : o;
-                }
-                bool seeds_later = false;
-#pragma unroll
-                for (int q = 0; q < 13; ++q) {
-                    bool push = false;
-                    unsigned mnode = n;
-                    if (act) {
-                        if (q < 12) {
-                            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
-                            if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
-                                mnode = (unsigned)(jj * nx + ii);
-                                const T tm = tf[mnode];
-                                if (!neg_bit(tm)) {
-                                    if (tm < inf) push = changed && lo <= tm;
-                                    else if (inband) push = true;
-                                    else seeds_later = true;
-                                }
-                            }
-                        } else {
-                            push = seeds_later && v < inf;
-                        }
-                        if (push) {
-                            const unsigned bit = 1u << (mnode & 31u);
-                            push = (atomicOr(bm + (mnode >> 5), bit) & bit) == 0u;
-                        }
-                    }
-                    const unsigned bp = __ballot_sync(FULL, push);
-                    if (push) LB[nc + __popc(bp & below)] = mnode;
-                    nc += __popc(bp);
-                }
-            }
-            __syncwarp();
-            nact = nc;
-            par ^= 1u;
-        }
+        unsigned rounds = 0u;
+        const bool ok = warp_sweep(g, nact, evals, rounds);
         if (lane == 0) {
+            if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
             atomicAdd(&a.q->visits, evals);
             atomicMax(&a.q->rounds, (unsigned long long)rounds);

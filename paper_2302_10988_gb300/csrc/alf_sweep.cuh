@@ -1,0 +1,209 @@
+// alf_sweep.cuh -- the round loop of the sweep for one grid, run by one warp
+// (the field-resident schedule and the near-source hierarchy share it).
+#pragma once
+
+#include "alf_internal.h"
+
+namespace alf {
+
+// order-preserving keys of non-negative times, and their warp minimum
+ALF_D unsigned order_key(float v) { return __float_as_uint(v); }  // v >= 0
+ALF_D unsigned long long order_key(double v) { return (unsigned long long)__double_as_longlong(v); }
+ALF_D float from_key(unsigned k, float) { return __uint_as_float(k); }
+ALF_D double from_key(unsigned long long k, double) { return __longlong_as_double((long long)k); }
+ALF_D unsigned warp_min(unsigned v) { return __reduce_min_sync(0xffffffffu, v); }
+ALF_D unsigned long long warp_min(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+
+// One grid swept by one warp: a field, or one level of the near-source hierarchy.
+template <typename T>
+struct WarpGrid {
+    T* tf;                      // times of the grid (frozen nodes carry the sign bit)
+    int nx, ny;
+    const uint16_t* map;        // region id of every node
+    const RegionP<T>* reg;      // region constants of the sample
+    T scale;                    // spacing of this grid / spacing of the regions' grid
+    unsigned* list0;            // dirty lists and evaluation list, nx * ny entries each
+    unsigned* list1;
+    unsigned* el;
+    T* ov;                      // time before / after each evaluation of a round
+    T* nv;
+    uint8_t* rec;               // records (may be null)
+    unsigned* bm;               // dirty bitmap, (nx * ny + 31) / 32 words (shared memory)
+    T band;                     // evaluation band beyond the front time
+    unsigned max_rounds;
+};
+
+// clears the bitmap and makes the non-frozen nodes of the square of half-width r around (ci, cj) the first dirty
+// set; returns its size
+template <typename T>
+ALF_D unsigned warp_seed_square(const WarpGrid<T>& g, int ci, int cj, int r)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned words = (unsigned)((g.nx * g.ny + 31) / 32);
+    for (unsigned w = lane; w < words; w += 32u) g.bm[w] = 0u;
+    __syncwarp();
+    unsigned nact = 0u;
+    const int w = 2 * r + 1;
+    for (int base = 0; base < w * w; base += 32) {
+        const int k = base + (int)lane;
+        bool take = false;
+        unsigned n = 0u;
+        if (k < w * w) {
+            const int i = ci + k % w - r, j = cj + k / w - r;
+            if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
+                n = (unsigned)(j * g.nx + i);
+                take = !neg_bit(g.tf[n]);
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, take);
+        if (take) {
+            g.list0[nact + __popc(bal & below)] = n;
+            atomicOr(g.bm + (n >> 5), 1u << (n & 31u));
+        }
+        nact += __popc(bal);
+    }
+    __syncwarp();
+    return nact;
+}
+
+// rounds of one grid to its fixed point; returns the evaluations, writes the rounds taken, false when the
+// round cap was reached
+template <typename T>
+ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    const T inf = alf_inf<T>();
+    const int nx = g.nx, ny = g.ny;
+    T* const tf = g.tf;
+    unsigned par = 0u;
+    rounds = 0u;
+    evals = 0ull;
+    while (nact != 0u) {
+        if (++rounds > g.max_rounds) return false;
+        const unsigned* LA = par ? g.list1 : g.list0;
+        unsigned* LB = par ? g.list0 : g.list1;
+        // front time of the dirty set and the band limit
+        auto m = order_key(inf);
+        for (unsigned k = lane; k < nact; k += 32u) {
+            const auto v = order_key(tf[LA[k]]);
+            m = v < m ? v : m;
+        }
+        const T lim = from_key(warp_min(m), T(0)) + g.band;
+        // split: in-band (or still unknown) nodes are evaluated, the rest wait
+        unsigned ne = 0u, nc = 0u;
+        for (unsigned base = 0; base < nact; base += 32u) {
+            const unsigned k = base + lane;
+            const bool in = k < nact;
+            bool ev = false;
+            unsigned n = 0u;
+            if (in) {
+                n = LA[k];
+                const T t = tf[n];
+                ev = t <= lim || !(t < inf);
+            }
+            const unsigned be = __ballot_sync(FULL, in && ev), bc = __ballot_sync(FULL, in && !ev);
+            if (in && ev) {
+                g.el[ne + __popc(be & below)] = n;
+                atomicAnd(g.bm + (n >> 5), ~(1u << (n & 31u)));
+            } else if (in) {
+                LB[nc + __popc(bc & below)] = n;
+            }
+            ne += __popc(be);
+            nc += __popc(bc);
+        }
+        __syncwarp();
+        // evaluate F at the in-band nodes (times updated in place)
+        for (unsigned e = lane; e < ne; e += 32u) {
+            const unsigned n = g.el[e];
+            const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+            T nb[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
+            }
+            const T old = tf[n];
+            RegionP<T> R = g.reg[__ldg(g.map + n)];
+            if (g.scale != T(1)) {
+                R.h *= g.scale;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) R.fb[c] *= g.scale;
+            }
+            int rc;
+            const T v = local_F<T>(nb, (int)n, nx, R, rc);
+            if (g.rec) g.rec[n] = (uint8_t)rc;
+            if (!same_bits(v, old)) tf[n] = v;
+            g.ov[e] = old;
+            g.nv[e] = v;
+        }
+        evals += ne;
+        __syncwarp();
+        // marking: changed nodes wake their later known neighbours; in-band nodes seed
+        // their unknown neighbours; an out-of-band node with unknown neighbours waits
+        for (unsigned base = 0; base < ne; base += 32u) {
+            const unsigned e = base + lane;
+            bool changed = false, inband = false, act = false;
+            unsigned n = 0u;
+            int i = 0, j = 0;
+            T v = inf, lo = inf;
+            if (e < ne) {
+                const T o = g.ov[e];
+                v = g.nv[e];
+                changed = !same_bits(o, v);
+                inband = v <= lim;
+                act = changed || inband;
+                n = g.el[e];
+                i = (int)(n % (unsigned)nx);
+                j = (int)(n / (unsigned)nx);
+                lo = v < o ? v : o;
+            }
+            bool seeds_later = false;
+#pragma unroll
+            for (int q = 0; q < 13; ++q) {
+                bool push = false;
+                unsigned mnode = n;
+                if (act) {
+                    if (q < 12) {
+                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                        if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
+                            mnode = (unsigned)(jj * nx + ii);
+                            const T tm = tf[mnode];
+                            if (!neg_bit(tm)) {
+                                if (tm < inf) push = changed && lo <= tm;
+                                else if (inband) push = true;
+                                else seeds_later = true;
+                            }
+                        }
+                    } else {
+                        push = seeds_later && v < inf;
+                    }
+                    if (push) {
+                        const unsigned bit = 1u << (mnode & 31u);
+                        push = (atomicOr(g.bm + (mnode >> 5), bit) & bit) == 0u;
+                    }
+                }
+                const unsigned bp = __ballot_sync(FULL, push);
+                if (push) LB[nc + __popc(bp & below)] = mnode;
+                nc += __popc(bp);
+            }
+        }
+        __syncwarp();
+        nact = nc;
+        par ^= 1u;
+    }
+    return true;
+}
+
+}  // namespace alf
