@@ -109,10 +109,11 @@ typedef struct {
     int max_ray_points;     /* points per ray including both ends (default 512) */
     int max_rounds;         /* livelock guard: sweep rounds per field <= max_rounds * (nx + ny) (default 64) */
     int sweep;              /* sweep schedule: 1 = all fields advance in lockstep rounds, each round a few
-                               kernels over the whole batch (suits few large fields); 2 = one warp owns
-                               each field and runs all its rounds inside one launch (suits many fields;
-                               needs nx*ny/8 bytes of shared memory per warp, nx*ny <= 2^18);
-                               0 = choose (2 when it fits and the fields fill the GPU), default 0 */
+                               kernels over the whole batch; 2 = one warp owns each field and runs all
+                               its rounds inside one launch (suits many fields; needs nx*ny/8 bytes of
+                               shared memory per warp, nx*ny <= 2^18); 3 = one CTA owns each field,
+                               one launch (suits few large fields); 0 = choose (2 when it fits and the
+                               fields fill the GPU, else 3), default 0 */
     int ctas_per_sm;        /* reserved (0) */
     int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
     double band_cells;      /* sweep schedule: nodes later than the front by more than this many
@@ -169,7 +170,7 @@ alf_status alf_plan_destroy(alf_plan* plan);
 /* Node offset of field f in the packed times buffer; total_nodes for f = nfields. */
 size_t alf_plan_field_offset(const alf_plan* plan, int field);
 int alf_plan_nfields(const alf_plan* plan);
-/* Options in effect (after autotuning, if it ran); `sweep` is the schedule in use (1 or 2). */
+/* Options in effect (after autotuning, if it ran); `sweep` is the schedule in use (1, 2 or 3). */
 alf_status alf_plan_options(const alf_plan* plan, alf_options* out);
 
 /* Forward solve (Secs. 2, 4): for every field, the near-source initialisation
@@ -235,10 +236,10 @@ alf_status alf_sync_status(alf_plan* plan, void* stream, int32_t* worst);
 /* Work counters of the last alf_solve (synchronises `stream`). */
 typedef struct {
     uint64_t node_evaluations; /* evaluations of the local operator in the sweep */
-    uint64_t rounds;           /* sweep rounds (sweep 1: of the whole batch; sweep 2: of the slowest field) */
+    uint64_t rounds;           /* sweep rounds (sweep 1: of the whole batch; 2, 3: of the slowest field) */
     uint64_t nodes;            /* nodes of the plan */
     uint64_t eval_launches;    /* launches timed (option time_kernels = 1): the evaluation kernel of every
-                                  round (sweep 1) or the one field-resident sweep kernel (sweep 2) */
+                                  round (sweep 1) or the one field-resident sweep kernel (sweep 2, 3) */
     double eval_ms;            /* their device time, measured with CUDA events on the solve's stream */
     uint64_t kernel_launches;  /* kernel launches issued by the library so far (whole process) */
 } alf_stats;

@@ -297,7 +297,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     } else {
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
     }
-    if (opt.sweep < 0 || opt.sweep > 2) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1 or 2");
+    if (opt.sweep < 0 || opt.sweep > 3) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1, 2 or 3");
     if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 64) return fail(ctx, ALF_ERR_INVALID_ARG, "ctas_per_sm out of range");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
@@ -411,8 +411,15 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         return fail(ctx, ALF_ERR_UNSUPPORTED, "sweep = 2: a field of %zu nodes does not fit the field-resident sweep",
                     p->max_field_nodes);
     }
+    // CTA-per-field sweep: shared bitmap when the largest field's fits in 64 KB, else global bitmaps
+    p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
+    if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
+    {
+        const int c = fim_cta_ctas_per_sm(opt.precision, p->cta_words);
+        p->cta_grid = std::max(1, c) * ctx->nsm;
+    }
     p->sweep_mode = opt.sweep != 0 ? opt.sweep
-                    : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 1;
+                    : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 3;
     // launch shapes of the sweep: one warp per field for the per-field steps, a
     // persistent-sized grid for the flat evaluation and marking steps
     p->grid_fields = std::max(1, std::min((p->nfields + 7) / 8, ctx->nsm * 16));
@@ -646,7 +653,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     a.band_cells = p->opt.band_cells;
     a.q = p->d_q;
     a.records = records;
-    if (p->sweep_mode == 2) {
+    if (p->sweep_mode == 2 || p->sweep_mode == 3) {
         // field-resident sweep: the whole fixed-point iteration in one launch
         const bool timing = p->opt.time_kernels != 0;
         if (timing && p->ev.size() < 2) {
@@ -654,7 +661,8 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
             for (auto& e : p->ev) ALF_CUDA(ctx, cudaEventCreate(&e));
         }
         if (timing) ALF_CUDA(ctx, cudaEventRecord(p->ev[0], st));
-        ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
+        if (p->sweep_mode == 2) ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
+        else ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, st));
         if (timing) {
             ALF_CUDA(ctx, cudaEventRecord(p->ev[1], st));
             ALF_CUDA(ctx, cudaEventSynchronize(p->ev[1]));
@@ -813,7 +821,7 @@ alf_status alf_plan_stats(alf_plan* p, void* stream, alf_stats* out)
     ALF_CUDA(ctx, cudaMemcpyAsync(p->h_q, p->d_q, sizeof(QueueState), cudaMemcpyDeviceToHost, st));
     ALF_CUDA(ctx, cudaStreamSynchronize(st));
     out->node_evaluations = p->h_q->visits;
-    out->rounds = p->sweep_mode == 2 ? p->h_q->rounds : p->sweep_rounds;
+    out->rounds = p->sweep_mode != 1 ? p->h_q->rounds : p->sweep_rounds;
     out->nodes = (uint64_t)p->total_nodes;
     out->eval_launches = p->eval_launches;
     out->eval_ms = p->eval_ms;
@@ -835,12 +843,15 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
         int block;
     };
     std::vector<Cand> cands;
-    const bool try1 = p->opt.sweep != 2, try2 = p->opt.sweep != 1 && p->warp_grid > 0;
+    const bool try1 = p->opt.sweep == 0 || p->opt.sweep == 1;
+    const bool try2 = (p->opt.sweep == 0 || p->opt.sweep == 2) && p->warp_grid > 0;
     if (try1)
         for (double band : {2.0, 3.0, 4.0, 6.0})
             for (int blk : {128, 256}) cands.push_back({1, band, blk});
     if (try2)
         for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block});
+    if (p->opt.sweep == 0 || p->opt.sweep == 3)
+        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({3, band, p->eval_block});
     double best_ms = 1e30, best_band = p->opt.band_cells;
     int best_block = p->eval_block, best_mode = p->sweep_mode;
     cudaEvent_t e0, e1;

@@ -81,6 +81,10 @@ cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long lon
 cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* order, unsigned words_per_warp,
                             int grid, cudaStream_t st);
 int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp);  // 0: does not fit
+// field-resident sweep by a CTA per field (few large fields); bitmaps of up to smem_words words in shared memory
+cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                           cudaStream_t st);
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -229,7 +233,9 @@ struct alf_plan {
     unsigned long long* h_pending = nullptr;  // pinned
     int rounds_per_check = 32;
     // field-resident sweep (option sweep = 2, or chosen by sweep = 0)
-    int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field
+    int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field, 3: one CTA per field
+    unsigned cta_words = 0;         // shared bitmap words of the CTA-per-field sweep
+    int cta_grid = 0;
     unsigned warp_words = 0;        // dirty-bitmap words of the largest field
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size

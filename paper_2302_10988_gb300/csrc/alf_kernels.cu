@@ -497,6 +497,105 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
     }
 }
 
+// Field-resident sweep by a whole CTA (few large fields): the same rounds, block barriers between the
+// steps.  The dirty bitmap is in shared memory when the field's fits, else in the field's global bitmap.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fim_cta_kernel(FimLaunch a, const unsigned* order, unsigned smem_words)
+{
+    extern __shared__ unsigned s_cbm[];
+    __shared__ CtaSweepShared sh;
+    __shared__ unsigned s_f, s_err;
+    const T inf = alf_inf<T>();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_f = atomicAdd(&a.q->head, 1u);
+            s_err = ld_volatile(&a.q->error);
+        }
+        __syncthreads();
+        const unsigned fi = s_f, err = s_err;
+        __syncthreads();
+        if (fi >= (unsigned)a.nfields || err != 0u) return;
+        const unsigned f = __ldg(order + fi);
+        const FieldDesc fd = a.fields[f];
+        WarpGrid<T> g;
+        g.tf = (T*)a.times + fd.node_off;
+        g.nx = fd.nx;
+        g.ny = fd.ny;
+        g.map = a.region_map + fd.map_off;
+        g.reg = (const RegionP<T>*)a.regions + (size_t)fd.sample * a.nregions;
+        g.scale = T(1);
+        g.list0 = a.list[0] + fd.node_off;
+        g.list1 = a.list[1] + fd.node_off;
+        g.el = a.elist + fd.node_off;
+        g.ov = (T*)a.oldv + fd.node_off;
+        g.nv = (T*)a.newv + fd.node_off;
+        g.rec = a.records ? a.records + fd.node_off : nullptr;
+        const unsigned words = (unsigned)((fd.nx * fd.ny + 31) / 32);
+        g.bm = words <= smem_words ? s_cbm : a.bitmap + a.bm_off[f];
+        g.band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
+        g.max_rounds = a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny);
+        const unsigned nact = cta_seed_square<T, NT>(g, fd.si, fd.sj, a.box + 2, sh);
+        unsigned long long evals = 0ull;
+        unsigned rounds = 0u;
+        const bool ok = cta_sweep<T, NT>(g, nact, evals, rounds, sh);
+        if (threadIdx.x == 0) {
+            if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
+            a.rounds[f] = rounds;
+            atomicAdd(&a.q->visits, evals);
+            atomicMax(&a.q->rounds, (unsigned long long)rounds);
+        }
+        __syncthreads();
+    }
+}
+
+#define ALF_CTA_THREADS 256
+
+template <typename T>
+static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
+{
+    *smem = (size_t)smem_words * sizeof(unsigned);
+    if (*smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fim_cta_kernel<T, ALF_CTA_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)*smem);
+}
+
+template <typename T>
+static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                             cudaStream_t st)
+{
+    size_t smem = 0;
+    cudaError_t e = fim_cta_smem<T>(smem_words, &smem);
+    if (e != cudaSuccess) return e;
+    fim_cta_kernel<T, ALF_CTA_THREADS><<<grid, ALF_CTA_THREADS, smem, st>>>(a, order, smem_words);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                           cudaStream_t st)
+{
+    return precision == ALF_FP64 ? fim_cta_t<double>(a, order, smem_words, grid, st)
+                                 : fim_cta_t<float>(a, order, smem_words, grid, st);
+}
+
+template <typename T>
+static int fim_cta_occ(unsigned smem_words)
+{
+    size_t smem = 0;
+    if (fim_cta_smem<T>(smem_words, &smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, ALF_CTA_THREADS>, ALF_CTA_THREADS,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words)
+{
+    return precision == ALF_FP64 ? fim_cta_occ<double>(smem_words) : fim_cta_occ<float>(smem_words);
+}
+
 // dynamic shared memory of the field-resident sweep: one dirty bitmap per warp
 template <typename T>
 static cudaError_t fim_warp_smem(unsigned words_per_warp, size_t* smem)

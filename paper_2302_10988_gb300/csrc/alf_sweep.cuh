@@ -206,4 +206,203 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
     return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// The same rounds run by a whole CTA of NT threads on one grid (for few, large
+// fields): block barriers between the steps, list slots reserved per warp with
+// shared-memory counters.  The dirty bitmap is in shared or global memory.
+// ---------------------------------------------------------------------------
+struct CtaSweepShared {
+    unsigned cnt[2];       // evaluation / carried (then marked) list sizes of the round
+    unsigned long long kmin[32];
+};
+
+template <typename T>
+ALF_D unsigned reserve(unsigned* counter, bool take, unsigned below)
+{
+    // warp-aggregated slot reservation: returns this lane's slot (valid when take)
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned base = 0u;
+    if (bal != 0u) {
+        const int leader = __ffs(bal) - 1;
+        if ((int)lane == leader) base = atomicAdd(counter, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    return base + __popc(bal & below);
+}
+
+// clears the bitmap and seeds the square of half-width r around (ci, cj); returns the dirty-set size
+template <typename T, int NT>
+ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaSweepShared& sh)
+{
+    const unsigned below = (1u << (threadIdx.x & 31u)) - 1u;
+    const unsigned words = (unsigned)((g.nx * g.ny + 31) / 32);
+    for (unsigned w = threadIdx.x; w < words; w += NT) g.bm[w] = 0u;
+    if (threadIdx.x == 0) sh.cnt[1] = 0u;
+    __syncthreads();
+    const int w = 2 * r + 1;
+    for (int base = 0; base < w * w; base += NT) {
+        const int k = base + (int)threadIdx.x;
+        bool take = false;
+        unsigned n = 0u;
+        if (k < w * w) {
+            const int i = ci + k % w - r, j = cj + k / w - r;
+            if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
+                n = (unsigned)(j * g.nx + i);
+                take = !neg_bit(g.tf[n]);
+            }
+        }
+        const unsigned slot = reserve<T>(&sh.cnt[1], take, below);
+        if (take) {
+            g.list0[slot] = n;
+            atomicOr(g.bm + (n >> 5), 1u << (n & 31u));
+        }
+    }
+    __syncthreads();
+    const unsigned nact = sh.cnt[1];
+    __syncthreads();
+    return nact;
+}
+
+template <typename T, int NT>
+ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds,
+                     CtaSweepShared& sh)
+{
+    constexpr int NW = NT / 32;
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const T inf = alf_inf<T>();
+    const int nx = g.nx, ny = g.ny;
+    T* const tf = g.tf;
+    unsigned par = 0u;
+    rounds = 0u;
+    evals = 0ull;
+    while (nact != 0u) {
+        if (++rounds > g.max_rounds) return false;
+        const unsigned* LA = par ? g.list1 : g.list0;
+        unsigned* LB = par ? g.list0 : g.list1;
+        // front time of the dirty set
+        auto m = order_key(inf);
+        for (unsigned k = threadIdx.x; k < nact; k += NT) {
+            const auto v = order_key(tf[LA[k]]);
+            m = v < m ? v : m;
+        }
+        m = warp_min(m);
+        if (lane == 0) sh.kmin[wid] = (unsigned long long)m;
+        if (threadIdx.x == 0) {
+            sh.cnt[0] = 0u;
+            sh.cnt[1] = 0u;
+        }
+        __syncthreads();
+        auto mm = order_key(inf);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const auto v = (decltype(mm))sh.kmin[w];
+            mm = v < mm ? v : mm;
+        }
+        const T lim = from_key(mm, T(0)) + g.band;
+        // split
+        for (unsigned base = 0; base < nact; base += NT) {
+            const unsigned k = base + threadIdx.x;
+            const bool in = k < nact;
+            bool ev = false;
+            unsigned n = 0u;
+            if (in) {
+                n = LA[k];
+                const T t = tf[n];
+                ev = t <= lim || !(t < inf);
+            }
+            const unsigned se = reserve<T>(&sh.cnt[0], in && ev, below);
+            const unsigned sc = reserve<T>(&sh.cnt[1], in && !ev, below);
+            if (in && ev) {
+                g.el[se] = n;
+                atomicAnd(g.bm + (n >> 5), ~(1u << (n & 31u)));
+            } else if (in) {
+                LB[sc] = n;
+            }
+        }
+        __syncthreads();
+        const unsigned ne = sh.cnt[0];
+        // evaluate
+        for (unsigned e = threadIdx.x; e < ne; e += NT) {
+            const unsigned n = g.el[e];
+            const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+            T nb[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
+            }
+            const T old = tf[n];
+            RegionP<T> R = g.reg[__ldg(g.map + n)];
+            if (g.scale != T(1)) {
+                R.h *= g.scale;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) R.fb[c] *= g.scale;
+            }
+            int rc;
+            const T v = local_F<T>(nb, (int)n, nx, R, rc);
+            if (g.rec) g.rec[n] = (uint8_t)rc;
+            if (!same_bits(v, old)) tf[n] = v;
+            g.ov[e] = old;
+            g.nv[e] = v;
+        }
+        evals += ne;
+        __syncthreads();
+        // marking
+        for (unsigned base = 0; base < ne; base += NT) {
+            const unsigned e = base + threadIdx.x;
+            bool changed = false, inband = false, act = false;
+            unsigned n = 0u;
+            int i = 0, j = 0;
+            T v = inf, lo = inf;
+            if (e < ne) {
+                const T o = g.ov[e];
+                v = g.nv[e];
+                changed = !same_bits(o, v);
+                inband = v <= lim;
+                act = changed || inband;
+                n = g.el[e];
+                i = (int)(n % (unsigned)nx);
+                j = (int)(n / (unsigned)nx);
+                lo = v < o ? v : o;
+            }
+            bool seeds_later = false;
+#pragma unroll
+            for (int q = 0; q < 13; ++q) {
+                bool push = false;
+                unsigned mnode = n;
+                if (act) {
+                    if (q < 12) {
+                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                        if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
+                            mnode = (unsigned)(jj * nx + ii);
+                            const T tm = tf[mnode];
+                            if (!neg_bit(tm)) {
+                                if (tm < inf) push = changed && lo <= tm;
+                                else if (inband) push = true;
+                                else seeds_later = true;
+                            }
+                        }
+                    } else {
+                        push = seeds_later && v < inf;
+                    }
+                    if (push) {
+                        const unsigned bit = 1u << (mnode & 31u);
+                        push = (atomicOr(g.bm + (mnode >> 5), bit) & bit) == 0u;
+                    }
+                }
+                const unsigned slot = reserve<T>(&sh.cnt[1], push, below);
+                if (push) LB[slot] = mnode;
+            }
+        }
+        __syncthreads();
+        nact = sh.cnt[1];
+        __syncthreads();
+        par ^= 1u;
+    }
+    return true;
+}
+
 }  // namespace alf

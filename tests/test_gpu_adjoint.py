@@ -21,7 +21,7 @@ def _problem(nsamples=3, n=56):
     return wl, truth
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 2e-3)])
 def test_backward_matches_oracle(api, oracle, precision, tol, sweep):
     wl, truth = _problem()

@@ -30,7 +30,7 @@ def _oracle_hier(oracle, wl, b, s, dens=(27, 9, 3), rad=(1, 6, 13)):
     return tau, rec, fr.reshape(tau.shape)
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_hierarchy_matches_oracle(api, oracle, precision, tol, sweep):
     """Weld medium with sources on an edge, in a corner and inside (levels clipped on some sides or none)."""

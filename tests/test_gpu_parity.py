@@ -62,7 +62,7 @@ def test_homogeneous_ti_fp64(api, oracle, group):
     assert np.allclose(rt.cpu().numpy()[0, 0], tau[r[:, 1], r[:, 0]], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_weld_ragged_parity(api, oracle, precision, tol, sweep):
     wl = W.weld_single(n=100, h=0.5e-3, rg=5, seed=12, nsrc=3, nrec=5)
@@ -81,7 +81,7 @@ def test_weld_ragged_parity(api, oracle, precision, tol, sweep):
         print(f"{precision} band={band}: record flips {flips}")
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 def test_tiny_and_edge_grids(api, oracle, sweep):
     for (nx, ny, si, sj) in [(2, 2, 0, 0), (3, 7, 2, 6), (33, 9, 32, 0), (65, 17, 0, 16), (40, 40, 20, 20)]:
         rm = np.zeros((ny, nx), np.uint16)
@@ -121,7 +121,7 @@ def test_weld_256_fp64_and_fp32(api, oracle):
     assert mr64.max().item() < 1e-12 and int(fl64.sum()) == 0
 
 
-@pytest.mark.parametrize("sweep", [1, 2])
+@pytest.mark.parametrize("sweep", [1, 2, 3])
 def test_uneven_batch_fp32(api, oracle, sweep):
     wl = W.weld_batch(nsamples=5, nsrc=3, nrec=4, sizes=(64, 96, 128, 160))
     P, th, times, rt, rec = _solve(api, wl, "fp32", sweep=sweep)
@@ -175,7 +175,7 @@ def test_graph_stream_and_timing(api, oracle):
     assert st["eval_launches"] > 0 and st["eval_ms"] > 0 and st["kernel_launches"] > 0
     assert (t3 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
     opt = Pt.autotune(th)
-    assert opt.band_cells in (1.0, 2.0, 3.0, 4.0, 6.0) and opt.sweep in (1, 2)
+    assert opt.band_cells in (1.0, 2.0, 3.0, 4.0, 6.0) and opt.sweep in (1, 2, 3)
 
 
 def test_sweep_schedules_agree(api, oracle):
@@ -184,8 +184,9 @@ def test_sweep_schedules_agree(api, oracle):
     wl = W.weld_batch(nsamples=6, nsrc=4, nrec=4, sizes=(32, 64, 96, 128))
     P1, th, t1, _, rec1 = _solve(api, wl, "fp64", sweep=1)
     P2, _, t2, _, rec2 = _solve(api, wl, "fp64", sweep=2)
-    assert torch.equal(t1, t2)
-    assert torch.equal(rec1, rec2)
+    P3, _, t3, _, rec3 = _solve(api, wl, "fp64", sweep=3)
+    assert torch.equal(t1, t2) and torch.equal(t1, t3)
+    assert torch.equal(rec1, rec2) and torch.equal(rec1, rec3)
     for b, s in ((0, 0), (3, 2), (5, 3)):
         tau, orec, fr, M = oracle_field(oracle, wl, b, s)
         assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
