@@ -356,6 +356,26 @@ def main():
             plain[prec] = P1.total_nodes / (e0.elapsed_time(e1) / 3 * 1e-3)
             del P1, t1
         line["plain_nodes_per_s"] = plain
+        # large single medium: 2048 x 2048, 64 sources, 4096 receivers per source
+        wlL = W.weld_large()
+        PL = api.Plan(wlL, precision="fp32", device=local, max_ray_points=1024)
+        thL = PL.theta_tensor()
+        tL = PL.new_times()
+        PL.solve(thL, times=tL)
+        PL.trace_rays(thL, tL)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        PL.solve(thL, times=tL)
+        e1.record(stream)
+        PL.trace_rays(thL, tL)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        line["large_medium"] = {"config": "2048 x 2048, 0.1 mm, 100 x 100 regions, 64 sources x 4096 receivers, FP32",
+                                "nodes_per_s": PL.total_nodes / (e0.elapsed_time(e1) * 1e-3),
+                                "rays_per_s": PL.nfields * PL.nrec / (e1.elapsed_time(e2) * 1e-3),
+                                "sweep": PL.options.sweep, "status": PL.status()}
+        del PL, tL
         # gradient: 256 samples x 32 sources on 200 x 200, forward (records) + adjoint
         wl3, truth = W.weld_adjoint()
         P3 = api.Plan(wl3, precision="fp32", device=local, keep_records=1)
