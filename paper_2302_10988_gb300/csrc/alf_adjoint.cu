@@ -12,6 +12,9 @@
 //             stencils; FP64 central differences of the group speed for the
 //             fallback and the frozen nodes) and the in-degree of every
 //             node (how many later nodes use it);
+//   (everything the sweep touches per node -- weights, lambda, its
+//   contribution lambda * dtau/dtheta, in-degree -- sits in one 32-byte
+//   record (64 bytes in FP64), one DRAM sector per node visit);
 //   seed      lambda = dL/dT at the receivers;
 //   rounds    Kahn's order: a node whose users have all been processed is
 //             final; it adds lambda * weight to the nodes it used and releases
@@ -19,7 +22,9 @@
 //             advance in lockstep rounds (a few launches per round), or one
 //             warp owns each field and runs all its rounds in one launch;
 //   reduce    dL/dtheta_region = sum over the region's nodes of
-//             lambda * d(time)/d(theta) (frozen nodes: the source's region).
+//             lambda * d(time)/d(theta) (frozen nodes: the source's region);
+//             the field-resident sweep sums them per warp in shared memory
+//             as it goes (regions <= 512), else a per-field block reduces.
 // Every node is processed exactly once, so the sweep is exact and its work is
 // linear in the number of nodes.
 #include <algorithm>
@@ -29,10 +34,17 @@
 namespace alf {
 
 template <typename T>
-struct AdjW {
-    T w[3];   // d tau_D / d tau of the supporting nodes (stencil A, B, C; fallback: w[0] = 1)
-    T wt;     // d tau_D / d theta
+struct alignas(8 * sizeof(T)) AdjNode {
+    T w[3];           // d tau_D / d tau of the supporting nodes (stencil A, B, C; fallback: w[0] = 1)
+    T wt;             // d tau_D / d theta
+    T lam;            // dL / d tau_D
+    T gn;             // lam * wt (the node's contribution to its region's gradient)
+    unsigned indeg;   // later nodes that use this one, not yet processed
+    unsigned pad;
 };
+static_assert(sizeof(AdjNode<float>) == 32 && sizeof(AdjNode<double>) == 64, "one or two DRAM sectors per node");
+
+size_t adj_node_bytes(int precision) { return precision == ALF_FP64 ? sizeof(AdjNode<double>) : sizeof(AdjNode<float>); }
 
 // analytic partial derivatives of the stencil time (see stencil_time)
 template <typename T>
@@ -91,11 +103,12 @@ ALF_D bool frozen_at(const unsigned* bits, int box, const FieldDesc& fd, int i, 
 // the nodes of the record's formula, in the order of the weights
 ALF_D int support_slots(int rec, int s[3])
 {
+    s[0] = s[1] = s[2] = 0;
     if (rec < 32) {
         const int p = rec >> 1;
-        s[0] = kPairA[p];
-        s[1] = (rec & 1) ? kPairQ[p] : kPairP[p];
-        s[2] = (rec & 1) ? kPairP[p] : kPairQ[p];
+        s[0] = pair_a(p);
+        s[1] = (rec & 1) ? pair_q(p) : pair_p(p);
+        s[2] = (rec & 1) ? pair_p(p) : pair_q(p);
         return 3;
     }
     if (rec < 44) {
@@ -105,95 +118,116 @@ ALF_D int support_slots(int rec, int s[3])
     return 0;
 }
 
+// support nodes of node (i, j) of a field (ns = 0 when a record points outside the grid)
+ALF_D int support_nodes(int rec, int i, int j, int nx, int ny, unsigned m[3])
+{
+    int s[3];
+    int ns = support_slots(rec, s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int ii = i + slot_di(s[k]), jj = j + slot_dj(s[k]);
+        if (k < ns && (ii < 0 || jj < 0 || ii >= nx || jj >= ny)) ns = 0;
+        m[k] = (unsigned)(jj * nx + ii);
+    }
+    return ns;
+}
+
+// weights of every node and the in-degrees (the node records are zeroed before)
 template <typename T>
 __global__ void adj_weights_kernel(AdjLaunch a)
 {
-    const size_t total = a.total_nodes;
     const T* times = (const T*)a.times;
-    AdjW<T>* W = (AdjW<T>*)a.weights;
+    AdjNode<T>* A = (AdjNode<T>*)a.nodes;
     const RegionP<T>* regions = (const RegionP<T>*)a.regions;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-        // field of node g: binary search over the node offsets
-        int lo = 0, hi = a.nfields;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if ((size_t)a.fields[mid].node_off <= g) lo = mid; else hi = mid;
-        }
-        const FieldDesc fd = a.fields[lo];
-        const unsigned n = (unsigned)(g - (size_t)fd.node_off);
+    // blockIdx.y strides over the fields, blockIdx.x and the threads over a field's nodes
+    for (int f = blockIdx.y; f < a.nfields; f += gridDim.y) {
+        const FieldDesc fd = a.fields[f];
+        const unsigned N = (unsigned)(fd.nx * fd.ny);
         const int nx = fd.nx, ny = fd.ny;
-        const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-        const unsigned* fb = a.frozen_bits + (size_t)lo * frozen_words(a.box);
-        AdjW<T> w{};
-        if (frozen_at(fb, a.box, fd, i, j)) {
-            // straight-ray time from the source: derivative by the source orientation
-            if (i != fd.si || j != fd.sj) {
-                const int rs = a.region_map[fd.map_off + (long long)fd.sj * nx + fd.si];
-                const MatD m = a.mats[a.region_mat[rs]];
-                const double th = a.theta[(size_t)fd.sample * a.nregions + rs];
-                const double di = i - fd.si, dj = j - fd.sj;
-                const double dist = sqrt(di * di + dj * dj) * a.h[fd.sample];
-                const double dir = atan2(dj, di);
-                const double e = 1e-6;
-                w.wt = T((dist / group_speed64(m, a.group_model, dir - th - e) -
-                          dist / group_speed64(m, a.group_model, dir - th + e)) / (2.0 * e));
+        const unsigned* fb = a.frozen_bits + (size_t)f * frozen_words(a.box);
+        AdjNode<T>* An = A + fd.node_off;
+        for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+            const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+            T w0 = T(0), w1 = T(0), w2 = T(0), wt = T(0);
+            if (frozen_at(fb, a.box, fd, i, j)) {
+                // straight-ray time from the source: derivative by the source orientation
+                if (i != fd.si || j != fd.sj) {
+                    const int rs = a.region_map[fd.map_off + (long long)fd.sj * nx + fd.si];
+                    const MatD m = a.mats[a.region_mat[rs]];
+                    const double th = a.theta[(size_t)fd.sample * a.nregions + rs];
+                    const double di = i - fd.si, dj = j - fd.sj;
+                    const double dist = sqrt(di * di + dj * dj) * a.h[fd.sample];
+                    const double dir = atan2(dj, di);
+                    const double e = 1e-6;
+                    wt = T((dist / group_speed64(m, a.group_model, dir - th - e) -
+                            dist / group_speed64(m, a.group_model, dir - th + e)) / (2.0 * e));
+                }
+            } else {
+                const int rec = a.records[fd.node_off + n];
+                unsigned ms[3];
+                const int ns = support_nodes(rec, i, j, nx, ny, ms);
+                if (ns == 3) {
+                    int s[3];
+                    support_slots(rec, s);
+                    const T* tf = times + fd.node_off;
+                    const T tA = abs_(tf[ms[0]]), tB = abs_(tf[ms[1]]), tC = abs_(tf[ms[2]]);
+                    const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + a.region_map[fd.map_off + n]];
+                    T w[3];
+                    stencil_partials<T>(slot_di(s[0]), slot_dj(s[0]), slot_di(s[1]), slot_dj(s[1]), slot_di(s[2]),
+                                        slot_dj(s[2]), tA, tB, tC, R, w, wt);
+                    w0 = w[0];
+                    w1 = w[1];
+                    w2 = w[2];
+                } else if (ns == 1) {
+                    const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + a.region_map[fd.map_off + n]];
+                    const int q = rec - 32, cls = slot_cls(q);
+                    const T d = cls == 0 ? R.dfb[0] : cls == 1 ? R.dfb[1] : cls == 2 ? R.dfb[2] : R.dfb[3];
+                    w0 = T(1);
+                    wt = (q >= 8 ? T(2) : T(1)) * d;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k < ns) atomicAdd(&An[ms[k]].indeg, 1u);
             }
-            W[g] = w;
-            continue;
+            AdjNode<T>& r = An[n];
+            r.w[0] = w0;
+            r.w[1] = w1;
+            r.w[2] = w2;
+            r.wt = wt;
         }
-        const int rec = a.records[g];
-        int s[3];
-        int ns = support_slots(rec, s);
-        for (int k = 0; k < ns; ++k) {  // a record from another solve could point outside the grid
-            const int ii = i + kSlotDi[s[k]], jj = j + kSlotDj[s[k]];
-            if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) ns = 0;
-        }
-        if (ns == 3) {
-            const T* tf = times + fd.node_off;
-            T t3[3];
-            for (int k = 0; k < 3; ++k) t3[k] = abs_(tf[(j + kSlotDj[s[k]]) * nx + i + kSlotDi[s[k]]]);
-            const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + a.region_map[fd.map_off + n]];
-            stencil_partials<T>(kSlotDi[s[0]], kSlotDj[s[0]], kSlotDi[s[1]], kSlotDj[s[1]], kSlotDi[s[2]],
-                                kSlotDj[s[2]], t3[0], t3[1], t3[2], R, w.w, w.wt);
-        } else if (ns == 1) {
-            const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + a.region_map[fd.map_off + n]];
-            w.w[0] = T(1);
-            const int cls = kSlotClass[s[0]];
-            w.wt = (s[0] >= 8 ? T(2) : T(1)) * R.dfb[cls];
-        }
-        for (int k = 0; k < ns; ++k)
-            atomicAdd(a.indeg + fd.node_off + (j + kSlotDj[s[k]]) * nx + i + kSlotDi[s[k]], 1u);
-        W[g] = w;
     }
 }
 
 template <typename T>
 __global__ void adj_seed_kernel(AdjLaunch a, const T* dL_drec)
 {
+    AdjNode<T>* A = (AdjNode<T>*)a.nodes;
     const int total = a.nfields * a.nrec;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         const int f = k / a.nrec, r = k % a.nrec;
         const FieldDesc fd = a.fields[f];
         const int ri = a.rec_ij[((size_t)fd.sample * a.nrec + r) * 2];
         const int rj = a.rec_ij[((size_t)fd.sample * a.nrec + r) * 2 + 1];
-        atomicAdd((T*)a.lambda + fd.node_off + (long long)rj * fd.nx + ri, dL_drec[k]);
+        atomicAdd(&A[fd.node_off + (long long)rj * fd.nx + ri].lam, dL_drec[k]);
     }
 }
 
 // first frontier of every field: the nodes no later node uses (one warp per field)
+template <typename T>
 __global__ void adj_frontier_kernel(AdjLaunch a)
 {
     const unsigned lane = threadIdx.x & 31u;
+    const AdjNode<T>* A = (const AdjNode<T>*)a.nodes;
     const size_t nw = (size_t)gridDim.x * blockDim.x / 32;
     for (size_t f = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < (size_t)a.nfields; f += nw) {
         const FieldDesc fd = a.fields[f];
         const unsigned N = (unsigned)(fd.nx * fd.ny);
-        const unsigned* deg = a.indeg + fd.node_off;
+        const AdjNode<T>* An = A + fd.node_off;
         unsigned* list = a.list[0] + fd.node_off;
         unsigned cnt = 0;
         for (unsigned base = 0; base < N; base += 32u) {
             const unsigned n = base + lane;
-            const bool take = n < N && deg[n] == 0u;
+            const bool take = n < N && An[n].indeg == 0u;
             const unsigned bal = __ballot_sync(0xffffffffu, take);
             if (take) list[cnt + __popc(bal & ((1u << lane) - 1u))] = n;
             cnt += __popc(bal);
@@ -202,6 +236,20 @@ __global__ void adj_frontier_kernel(AdjLaunch a)
             a.cnt[f] = cnt;
             a.cnt[a.nfields + f] = 0u;
         }
+    }
+}
+
+// first frontier, one thread per node (field-resident schedule)
+template <typename T>
+__global__ void adj_frontier_flat_kernel(AdjLaunch a)
+{
+    const AdjNode<T>* A = (const AdjNode<T>*)a.nodes;
+    for (int f = blockIdx.y; f < a.nfields; f += gridDim.y) {
+        const FieldDesc fd = a.fields[f];
+        const unsigned N = (unsigned)(fd.nx * fd.ny);
+        const AdjNode<T>* An = A + fd.node_off;
+        for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+            if (An[n].indeg == 0u) a.list[0][fd.node_off + atomicAdd(a.cnt + f, 1u)] = n;
     }
 }
 
@@ -230,13 +278,12 @@ __global__ void adj_scan_kernel(AdjLaunch a, int parity)
     if (threadIdx.x == 1023) a.eoff[n] = s[1023];
 }
 
+// one Kahn round of every field (lockstep schedule): thread per frontier entry
 template <typename T>
 __global__ void adj_process_kernel(AdjLaunch a, int parity)
 {
     const unsigned E = a.eoff[a.nfields];
-    T* lam = (T*)a.lambda;
-    const AdjW<T>* W = (const AdjW<T>*)a.weights;
-    T* gnode = (T*)a.gnode;
+    AdjNode<T>* A = (AdjNode<T>*)a.nodes;
     unsigned* nxt = a.cnt + (size_t)(parity ^ 1) * a.nfields;
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
         int lo = 0, hi = a.nfields;
@@ -246,58 +293,43 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
         }
         const FieldDesc fd = a.fields[lo];
         const unsigned n = a.list[parity][fd.node_off + (e - a.eoff[lo])];
-        const size_t g = (size_t)fd.node_off + n;
-        const T l = lam[g];
-        const AdjW<T> w = W[g];
-        gnode[g] = l * w.wt;
+        AdjNode<T>* An = A + fd.node_off;
+        const T l = __ldcg(&An[n].lam);
+        const T w0 = An[n].w[0], w1 = An[n].w[1], w2 = An[n].w[2];
+        An[n].gn = l * An[n].wt;
         const unsigned* fbits = a.frozen_bits + (size_t)lo * frozen_words(a.box);
         const int nx = fd.nx;
         const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
         if (frozen_at(fbits, a.box, fd, i, j)) continue;
-        int s[3];
-        int ns = support_slots(a.records[g], s);
-        for (int k = 0; k < ns; ++k) {
-            const int ii = i + kSlotDi[s[k]], jj = j + kSlotDj[s[k]];
-            if (ii < 0 || jj < 0 || ii >= nx || jj >= fd.ny) ns = 0;
-        }
+        unsigned ms[3];
+        const int ns = support_nodes(a.records[fd.node_off + n], i, j, nx, fd.ny, ms);
         unsigned* list = a.list[parity ^ 1] + fd.node_off;
-        for (int k = 0; k < ns; ++k) {
-            const unsigned m = (unsigned)((j + kSlotDj[s[k]]) * nx + i + kSlotDi[s[k]]);
-            atomicAdd(lam + fd.node_off + m, l * w.w[k]);
-            __threadfence();
-            if (atomicSub(a.indeg + fd.node_off + m, 1u) == 1u) list[atomicAdd(nxt + lo, 1u)] = m;
-        }
-    }
-}
-
-// first frontier of every field, one thread per node (field-resident schedule)
-__global__ void adj_frontier_flat_kernel(AdjLaunch a)
-{
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total_nodes;
-         g += (size_t)gridDim.x * blockDim.x) {
-        if (a.indeg[g] != 0u) continue;
-        int lo = 0, hi = a.nfields;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if ((size_t)a.fields[mid].node_off <= g) lo = mid; else hi = mid;
-        }
-        const size_t off = (size_t)a.fields[lo].node_off;
-        a.list[0][off + atomicAdd(a.cnt + lo, 1u)] = (unsigned)(g - off);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k < ns) {
+                atomicAdd(&An[ms[k]].lam, l * (k == 0 ? w0 : k == 1 ? w1 : w2));
+                __threadfence();
+                if (atomicSub(&An[ms[k]].indeg, 1u) == 1u) list[atomicAdd(nxt + lo, 1u)] = ms[k];
+            }
     }
 }
 
 // Kahn rounds of one field by one warp, fields taken from a queue (largest first).  Only the owning
-// warp touches a field's lambda and in-degrees, and the warp barrier at the end of a round orders a
-// round's contributions before the next round reads them (through L2: __ldcg).
+// warp touches a field's node records, and the warp barrier at the end of a round orders a round's
+// contributions before the next round reads them (through L2: __ldcg).  With few regions the
+// warp sums the region gradients in shared memory as it goes.
 template <typename T>
-__global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a)
+__global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad, int smem_regions)
 {
+    extern __shared__ double s_acc[];
     constexpr unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
-    T* const lam = (T*)a.lambda;
-    const AdjW<T>* W = (const AdjW<T>*)a.weights;
-    T* const gnode = (T*)a.gnode;
+    double* acc = s_acc + (size_t)(threadIdx.x >> 5) * (smem_regions ? a.nregions : 0);
+    AdjNode<T>* const A = (AdjNode<T>*)a.nodes;
+    if (smem_regions)
+        for (int r = (int)lane; r < a.nregions; r += 32) acc[r] = 0.0;
+    __syncwarp();
     for (;;) {
         unsigned fi = 0u;
         if (lane == 0) fi = atomicAdd(a.head, 1u);
@@ -306,10 +338,12 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a)
         const unsigned f = __ldg(a.order + fi);
         const FieldDesc fd = a.fields[f];
         const int nx = fd.nx, ny = fd.ny;
-        const size_t off = (size_t)fd.node_off;
+        AdjNode<T>* const An = A + fd.node_off;
         const unsigned* fbits = a.frozen_bits + (size_t)f * frozen_words(a.box);
-        unsigned* const list0 = a.list[0] + off;
-        unsigned* const list1 = a.list[1] + off;
+        const uint16_t* map = a.region_map + fd.map_off;
+        const int rsrc = map[(long long)fd.sj * nx + fd.si];
+        unsigned* const list0 = a.list[0] + fd.node_off;
+        unsigned* const list1 = a.list[1] + fd.node_off;
         unsigned nact = a.cnt[f], par = 0u;
         while (nact != 0u) {
             const unsigned* LA = par ? list1 : list0;
@@ -317,43 +351,49 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a)
             unsigned nc = 0u;
             for (unsigned base = 0; base < nact; base += 32u) {
                 const unsigned e = base + lane;
-                unsigned m[3] = {0u, 0u, 0u};
+                unsigned ms[3] = {0u, 0u, 0u};
                 bool fresh[3] = {false, false, false};
                 if (e < nact) {
                     const unsigned n = LA[e];
-                    const size_t g = off + n;
-                    const T l = __ldcg(lam + g);
-                    const AdjW<T> w = W[g];
-                    gnode[g] = l * w.wt;
+                    const T l = __ldcg(&An[n].lam);
+                    const T w0 = An[n].w[0], w1 = An[n].w[1], w2 = An[n].w[2];
+                    const T g = l * An[n].wt;
                     const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                    if (!frozen_at(fbits, a.box, fd, i, j)) {
-                        int s[3];
-                        int ns = support_slots(a.records[g], s);
-                        for (int k = 0; k < ns; ++k) {
-                            const int ii = i + kSlotDi[s[k]], jj = j + kSlotDj[s[k]];
-                            if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) ns = 0;
-                        }
+                    const bool fz = frozen_at(fbits, a.box, fd, i, j);
+                    if (smem_regions) {
+                        if (g != T(0)) atomicAdd(acc + (fz ? rsrc : (int)map[n]), (double)g);
+                    } else {
+                        An[n].gn = g;
+                    }
+                    if (!fz) {
+                        const int ns = support_nodes(a.records[fd.node_off + n], i, j, nx, ny, ms);
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
-                            if (k < ns) {
-                                m[k] = (unsigned)((j + kSlotDj[s[k]]) * nx + i + kSlotDi[s[k]]);
-                                atomicAdd(lam + off + m[k], l * w.w[k]);
-                            }
+                            if (k < ns) atomicAdd(&An[ms[k]].lam, l * (k == 0 ? w0 : k == 1 ? w1 : w2));
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
-                            if (k < ns) fresh[k] = atomicSub(a.indeg + off + m[k], 1u) == 1u;
+                            if (k < ns) fresh[k] = atomicSub(&An[ms[k]].indeg, 1u) == 1u;
                     }
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const unsigned b = __ballot_sync(FULL, fresh[k]);
-                    if (fresh[k]) LB[nc + __popc(b & below)] = m[k];
+                    if (fresh[k]) LB[nc + __popc(b & below)] = ms[k];
                     nc += __popc(b);
                 }
             }
             __syncwarp();
             nact = nc;
             par ^= 1u;
+        }
+        if (smem_regions) {
+            // flush this field's region sums
+            double* gb = grad + (size_t)fd.sample * a.nregions;
+            for (int r = (int)lane; r < a.nregions; r += 32) {
+                if (acc[r] != 0.0) atomicAdd(gb + r, acc[r]);
+                acc[r] = 0.0;
+            }
+            __syncwarp();
         }
     }
 }
@@ -369,13 +409,13 @@ __global__ void adj_reduce_kernel(AdjLaunch a, double* grad)
     if (use_smem)
         for (int r = threadIdx.x; r < a.nregions; r += blockDim.x) acc[r] = 0.0;
     __syncthreads();
-    const T* gnode = (const T*)a.gnode + fd.node_off;
+    const AdjNode<T>* An = (const AdjNode<T>*)a.nodes + fd.node_off;
     const unsigned* fbits = a.frozen_bits + (size_t)f * frozen_words(a.box);
     const int rs = a.region_map[fd.map_off + (long long)fd.sj * fd.nx + fd.si];
     double* gb = grad + (size_t)fd.sample * a.nregions;
     const int N = fd.nx * fd.ny;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const T v = gnode[n];
+        const T v = An[n].gn;
         if (v == T(0)) continue;
         const int i = n % fd.nx, j = n / fd.nx;
         const int r = frozen_at(fbits, a.box, fd, i, j) ? rs : a.region_map[fd.map_off + n];
@@ -402,25 +442,30 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
                              unsigned long long* h_pending, int grid, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.lambda, 0, a.total_nodes * sizeof(T), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.indeg, 0, a.total_nodes * sizeof(unsigned), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.gnode, 0, a.total_nodes * sizeof(T), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.nodes, 0, a.total_nodes * sizeof(AdjNode<T>), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(grad, 0, (size_t)a.nsamples * a.nregions * sizeof(double), st)) != cudaSuccess) return e;
-    adj_weights_kernel<T><<<grid, 256, 0, st>>>(a);
+    const dim3 fgrid(8, (unsigned)std::min(a.nfields, 65535));
+    adj_weights_kernel<T><<<fgrid, 256, 0, st>>>(a);
     adj_seed_kernel<T><<<64, 256, 0, st>>>(a, (const T*)dL_drec);
+    note_launches(2);
     if (a.warp_grid > 0) {
         // field-resident schedule: flat frontier, then every field's rounds in one launch
         if ((e = cudaMemsetAsync(a.cnt, 0, (size_t)a.nfields * sizeof(unsigned), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(a.head, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-        adj_frontier_flat_kernel<<<grid, 256, 0, st>>>(a);
-        adj_warp_kernel<T><<<a.warp_grid, 256, 0, st>>>(a);
-        const size_t smem = a.nregions <= 4096 ? (size_t)a.nregions * sizeof(double) : 0;
-        adj_reduce_kernel<T><<<a.nfields, 256, smem, st>>>(a, grad);
-        note_launches(5);
+        adj_frontier_flat_kernel<T><<<fgrid, 256, 0, st>>>(a);
+        const int smem_regions = a.nregions <= 512 ? 1 : 0;
+        const size_t smem = smem_regions ? (size_t)8 * a.nregions * sizeof(double) : 0;
+        adj_warp_kernel<T><<<a.warp_grid, 256, smem, st>>>(a, grad, smem_regions);
+        note_launches(2);
+        if (!smem_regions) {
+            const size_t rs = a.nregions <= 4096 ? (size_t)a.nregions * sizeof(double) : 0;
+            adj_reduce_kernel<T><<<a.nfields, 256, rs, st>>>(a, grad);
+            note_launches(1);
+        }
         return cudaGetLastError();
     }
-    adj_frontier_kernel<<<std::max(1, std::min((a.nfields + 7) / 8, grid)), 256, 0, st>>>(a);
-    note_launches(3);
+    adj_frontier_kernel<T><<<std::max(1, std::min((a.nfields + 7) / 8, grid)), 256, 0, st>>>(a);
+    note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int parity = 0;
     for (long long r = 0; r < (long long)a.max_rounds;) {

@@ -235,10 +235,7 @@ static void plan_free(alf_plan* p)
     dfree(p->d_adj_head);
     dfree(p->d_hier);
     dfree(p->d_hier_head);
-    dfree(p->d_adj_w);
-    dfree(p->d_lambda);
-    dfree(p->d_gnode);
-    dfree(p->d_indeg);
+    dfree(p->d_adj_nodes);
     dfree(p->d_list0);
     dfree(p->d_list1);
     dfree(p->d_elist);
@@ -482,16 +479,8 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     ALLOC(p->d_bitmap, p->bm_words);
     if (opt.keep_records) {
         char* w = nullptr;
-        char* l = nullptr;
-        char* gn = nullptr;
-        const size_t tb = opt.precision == ALF_FP64 ? 8 : 4;
-        ALLOC(w, p->total_nodes * 4 * tb);
-        p->d_adj_w = w;
-        ALLOC(l, p->total_nodes * tb);
-        p->d_lambda = l;
-        ALLOC(gn, p->total_nodes * tb);
-        p->d_gnode = gn;
-        ALLOC(p->d_indeg, p->total_nodes);
+        ALLOC(w, p->total_nodes * adj_node_bytes(opt.precision));
+        p->d_adj_nodes = w;
     }
     ALLOC(p->d_bm_off, (size_t)p->nfields);
     ALLOC(p->d_cnt, 2 * (size_t)p->nfields);
@@ -743,7 +732,7 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
     alf_ctx* ctx = p->ctx;
     if (!theta || !times || !records || !dL_drec || !dL_dtheta)
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: null pointer");
-    if (!p->opt.keep_records || !p->d_adj_w)
+    if (!p->opt.keep_records || !p->d_adj_nodes)
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: the plan was created without keep_records");
     if (p->opt.init_mode != ALF_INIT_RADIUS)
         return fail(ctx, ALF_ERR_UNSUPPORTED, "alf_backward: only the straight-ray initialisation is differentiated");
@@ -772,10 +761,7 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
     a.frozen_bits = p->d_frozen;
     a.records = records;
     a.rec_ij = p->d_rec;
-    a.weights = p->d_adj_w;
-    a.lambda = p->d_lambda;
-    a.gnode = p->d_gnode;
-    a.indeg = p->d_indeg;
+    a.nodes = p->d_adj_nodes;
     a.list[0] = p->d_list0;
     a.list[1] = p->d_list1;
     a.cnt = p->d_cnt;

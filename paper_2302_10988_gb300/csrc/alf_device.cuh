@@ -151,6 +151,51 @@ ALF_HD constexpr int pa(int p) { constexpr int t[16] = {4, 6, 7, 5, 8, 11, 10, 9
 ALF_HD constexpr int pp(int p) { constexpr int t[16] = {2, 3, 1, 1, 4, 7, 5, 7, 3, 2, 2, 3, 0, 1, 1, 0}; return t[p]; }
 ALF_HD constexpr int pq(int p) { constexpr int t[16] = {0, 0, 3, 2, 6, 6, 4, 5, 7, 5, 4, 6, 6, 7, 5, 4}; return t[p]; }
 
+// Run-time lookups of the slot and pair tables (index known only at run time, e.g. from a
+// record): fields packed into 64-bit immediates and extracted with shifts, so that lanes with
+// different indices neither touch memory nor serialise on the constant cache.
+ALF_HD constexpr unsigned long long pack_bits(int which, int bits)
+{
+    unsigned long long v = 0ull;
+    const int n = which < 3 ? 12 : 16;
+    for (int k = 0; k < n; ++k) {
+        const int x = which == 0 ? sdi(k) + 2 : which == 1 ? sdj(k) + 2 : which == 2 ? scls(k)
+                    : which == 3 ? pa(k) : which == 4 ? pp(k) : pq(k);
+        v |= (unsigned long long)x << (bits * k);
+    }
+    return v;
+}
+ALF_HD int slot_di(int k)
+{
+    constexpr unsigned long long t = pack_bits(0, 3);
+    return (int)((t >> (3 * k)) & 7ull) - 2;
+}
+ALF_HD int slot_dj(int k)
+{
+    constexpr unsigned long long t = pack_bits(1, 3);
+    return (int)((t >> (3 * k)) & 7ull) - 2;
+}
+ALF_HD int slot_cls(int k)
+{
+    constexpr unsigned long long t = pack_bits(2, 2);
+    return (int)((t >> (2 * k)) & 3ull);
+}
+ALF_HD int pair_a(int p)
+{
+    constexpr unsigned long long t = pack_bits(3, 4);
+    return (int)((t >> (4 * p)) & 15ull);
+}
+ALF_HD int pair_p(int p)
+{
+    constexpr unsigned long long t = pack_bits(4, 4);
+    return (int)((t >> (4 * p)) & 15ull);
+}
+ALF_HD int pair_q(int p)
+{
+    constexpr unsigned long long t = pack_bits(5, 4);
+    return (int)((t >> (4 * p)) & 15ull);
+}
+
 // ---------------------------------------------------------------------------
 // The local operator F at node D (linear index `me`; the tie order of equal
 // times is the linear index, which for diamond neighbours is the static order

@@ -142,10 +142,7 @@ struct AdjLaunch {
     const unsigned* frozen_bits;
     const uint8_t* records;
     const int32_t* rec_ij;
-    void* weights;    // per node: 3 support weights + orientation weight (T)
-    void* lambda;     // per node (T)
-    void* gnode;      // per node: lambda * d tau / d theta (T)
-    unsigned* indeg;  // per node
+    void* nodes;      // per node: AdjNode<T> (weights, lambda, lambda * dtau/dtheta, in-degree)
     unsigned* list[2];
     unsigned* cnt;    // [2][nfields]
     unsigned* eoff;   // [nfields + 1]
@@ -156,6 +153,7 @@ struct AdjLaunch {
     unsigned* head;
     int warp_grid;
 };
+size_t adj_node_bytes(int precision);
 cudaError_t launch_adjoint(int precision, const AdjLaunch& a, const void* dL_drec, double* grad,
                            unsigned long long* d_pending, unsigned long long* h_pending, int grid, cudaStream_t st);
 
@@ -256,10 +254,7 @@ struct alf_plan {
     double eval_ms = 0.0;
     unsigned long long eval_launches = 0, sweep_rounds = 0;
     // adjoint workspace (keep_records = 1)
-    void* d_adj_w = nullptr;
-    void* d_lambda = nullptr;
-    void* d_gnode = nullptr;
-    unsigned* d_indeg = nullptr;
+    void* d_adj_nodes = nullptr;    // AdjNode<T> per node (32 B FP32, 64 B FP64)
     alf::QueueState* d_q = nullptr;
     unsigned* d_ray_error = nullptr;
     unsigned* d_frozen = nullptr;  // per-field bitmap of frozen nodes in the source box

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(NT) fim_eval_kernel(FimLaunch a)
         T nb[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
-            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+            const int ii = i + sdi(q), jj = j + sdj(q);
             nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? __ldcg(tf + jj * nx + ii) : alf_inf<T>();
         }
         const T old = __ldcg(tf + n);
@@ -407,7 +407,7 @@ __global__ void fim_mark_kernel(FimLaunch a, int parity)
         bool seeds_later = false;
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
-            const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+            const int ii = i + sdi(q), jj = j + sdj(q);
             if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
             const unsigned m = (unsigned)(jj * nx + ii);
             const T tm = __ldcg(tf + m);

@@ -131,7 +131,7 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
             T nb[12];
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                const int ii = i + sdi(q), jj = j + sdj(q);
                 nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
             }
             const T old = tf[n];
@@ -176,7 +176,7 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
                 unsigned mnode = n;
                 if (act) {
                     if (q < 12) {
-                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                        const int ii = i + sdi(q), jj = j + sdj(q);
                         if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
                             mnode = (unsigned)(jj * nx + ii);
                             const T tm = tf[mnode];
@@ -331,7 +331,7 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
             T nb[12];
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
-                const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                const int ii = i + sdi(q), jj = j + sdj(q);
                 nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
             }
             const T old = tf[n];
@@ -375,7 +375,7 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                 unsigned mnode = n;
                 if (act) {
                     if (q < 12) {
-                        const int ii = i + kSlotDi[q], jj = j + kSlotDj[q];
+                        const int ii = i + sdi(q), jj = j + sdj(q);
                         if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
                             mnode = (unsigned)(jj * nx + ii);
                             const T tm = tf[mnode];
