@@ -39,7 +39,8 @@ ALF_D double group_speed_T<float>(const MatD& m, const RegionP<float>& R, int mo
 
 template <typename T>
 struct RayCtx {
-    const FieldDesc* fd;
+    int nx, ny;
+    long long map_off;
     const uint16_t* map;
     const uint16_t* region_mat;
     const MatD* mats;
@@ -53,20 +54,31 @@ template <typename T>
 ALF_D int node_at(const RayCtx<T>& c, T x, T y)
 {
     int i = (int)floor((double)x + 0.5), j = (int)floor((double)y + 0.5);
-    i = min(max(i, 0), c.fd->nx - 1);
-    j = min(max(j, 0), c.fd->ny - 1);
-    return j * c.fd->nx + i;
+    i = min(max(i, 0), c.nx - 1);
+    j = min(max(j, 0), c.ny - 1);
+    return j * c.nx + i;
 }
 
-// straight-ray time of length len (cells) along direction dir through node n
+// direction angle of (sx, sy) relative to the orientation th: FP32 atan2 on the FP32 path (the
+// ray's own precision; the FP64 pipe is slow on this part), FP64 on the FP64 path
+ALF_D double rel_dir(float sx, float sy, double th) { return (double)(atan2f(sy, sx) - (float)th); }
+ALF_D double rel_dir(double sx, double sy, double th) { return atan2(sy, sx) - th; }
+
+// straight-ray time of length len (cells) along (sx, sy) through node n
 template <typename T>
-ALF_D T piece_time(const RayCtx<T>& c, int n, T len, double dir)
+ALF_D T piece_time(const RayCtx<T>& c, int n, T len, T sx, T sy)
 {
-    const int r = c.map[c.fd->map_off + n];
-    const MatD m = c.mats[c.region_mat[r]];
-    const double V = group_speed_T<T>(m, c.regions[r], c.model, dir - c.theta[r]);
+    const int r = c.map[c.map_off + n];
+    const MatD& m = c.mats[c.region_mat[r]];  // by reference: no local copy for the FP64 fallbacks
+    const double V = group_speed_T<T>(m, c.regions[r], c.model, rel_dir(sx, sy, c.theta[r]));
     return T((double)len * c.h / V);
 }
+
+// plane families: x = c, y = c, x - y = c, x + y = c; normal (fam_nx, fam_ny) and node step along the plane
+ALF_D int fam_nx(int k) { return k == 1 ? 0 : 1; }
+ALF_D int fam_ny(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? -1 : 1; }
+ALF_D int fam_tx(int k) { return k == 0 ? 0 : 1; }
+ALF_D int fam_ty(int k) { return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 1 : -1; }
 
 template <typename T>
 __global__ void ray_kernel(RayLaunch a)
@@ -78,7 +90,9 @@ __global__ void ray_kernel(RayLaunch a)
     const FieldDesc fd = a.fields[f];
     const int b = fd.sample;
     RayCtx<T> c;
-    c.fd = &fd;
+    c.nx = fd.nx;
+    c.ny = fd.ny;
+    c.map_off = fd.map_off;
     c.map = a.region_map;
     c.region_mat = a.region_mat;
     c.mats = a.mats;
@@ -97,11 +111,6 @@ __global__ void ray_kernel(RayLaunch a)
     pts[1] = by;
     np = 1;
     int status = 1;
-    // plane families: normal and node step along the plane
-    const int NX[4] = {1, 0, 1, 1}, NY[4] = {0, 1, -1, 1};
-    const int TXs[4] = {0, 1, 1, 1}, TYs[4] = {1, 0, 1, -1};
-    T cost[33];
-    int pidx[33];
     while (np < a.max_pts) {
         const T rx = xt - bx, ry = yt - by;
         if (sqrt_(rx * rx + ry * ry) < T(a.stop_radius)) {
@@ -114,15 +123,16 @@ __global__ void ray_kernel(RayLaunch a)
         const T dl = sqrt_(dx * dx + dy * dy);
         int fam = 0;
         T bestc = T(-1);
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const T nl = sqrt_(T(NX[k] * NX[k] + NY[k] * NY[k]));
-            const T cs = abs_(dx * T(NX[k]) + dy * T(NY[k])) / (dl * nl);
+            const T nl = sqrt_(T(fam_nx(k) * fam_nx(k) + fam_ny(k) * fam_ny(k)));
+            const T cs = abs_(dx * T(fam_nx(k)) + dy * T(fam_ny(k))) / (dl * nl);
             if (cs > bestc + T(1e-12)) {
                 bestc = cs;
                 fam = k;
             }
         }
-        const T nxf = T(NX[fam]), nyf = T(NY[fam]);
+        const T nxf = T(fam_nx(fam)), nyf = T(fam_ny(fam));
         const T qB = nxf * bx + nyf * by, qT = nxf * xt + nyf * yt;
         const T dn = dx * nxf + dy * nyf;
         const T sg = dn >= T(0) ? T(1) : T(-1);
@@ -152,10 +162,32 @@ __global__ void ray_kernel(RayLaunch a)
             bxn = T(0);
             byn = qn;
         }
-        const T stx = T(TXs[fam]), sty = T(TYs[fam]);
+        const T stx = T(fam_tx(fam)), sty = T(fam_ty(fam));
         const T pc = fam == 0 ? py : px;
         const int p0 = (int)floor((double)pc + 0.5);
-        int nc = 0;
+        // candidates streamed in order of p: every local minimum (with its neighbours when they are
+        // consecutive candidates) is refined by a parabola as soon as its right neighbour is known
+        T best = alf_inf<T>();
+        T bpos = T(0);
+        T c1 = alf_inf<T>(), c2 = alf_inf<T>();
+        int p1 = 0, p2 = 0, nv = 0;
+        auto consider = [&](T cl, bool cl_ok, T ck, int pk, T cr, bool cr_ok) {
+            if (!cl_ok) cl = alf_inf<T>();
+            if (!cr_ok) cr = alf_inf<T>();
+            if (!(ck < cl && ck <= cr)) return;
+            T val = ck, off = T(0);
+            if (cl_ok && cr_ok) {
+                const T den = cl - T(2) * ck + cr;
+                if (den > T(0)) {
+                    off = (cl - cr) / (T(2) * den);
+                    val = ck - (cl - cr) * (cl - cr) / (T(8) * den);
+                }
+            }
+            if (val < best) {
+                best = val;
+                bpos = T(pk) + off;
+            }
+        };
         for (int p = p0 - a.halfwidth; p <= p0 + a.halfwidth; ++p) {
             const T cx = bxn + T(p) * stx, cy = byn + T(p) * sty;
             const int ci = (int)cx, cj = (int)cy;
@@ -167,34 +199,18 @@ __global__ void ray_kernel(RayLaunch a)
             T seg = T(0);
             if (len > T(0)) {
                 const int mn = node_at(c, T(0.5) * (bx + cx), T(0.5) * (by + cy));
-                seg = piece_time(c, mn, len, atan2((double)sy, (double)sx));
+                seg = piece_time(c, mn, len, sx, sy);
             }
-            cost[nc] = seg + tc;
-            pidx[nc] = p;
-            nc++;
+            const T cost = seg + tc;
+            if (nv >= 1) consider(c1, nv >= 2 && p1 == p2 - 1, c2, p2, cost, p == p2 + 1);
+            c1 = c2;
+            p1 = p2;
+            c2 = cost;
+            p2 = p;
+            nv++;
         }
-        if (nc == 0) break;
-        T best = alf_inf<T>();
-        T bpos = T(0);
-        for (int k = 0; k < nc; ++k) {
-            const bool cl_ok = k > 0 && pidx[k - 1] == pidx[k] - 1;
-            const bool cr_ok = k + 1 < nc && pidx[k + 1] == pidx[k] + 1;
-            const T cl = cl_ok ? cost[k - 1] : alf_inf<T>();
-            const T cr = cr_ok ? cost[k + 1] : alf_inf<T>();
-            if (!(cost[k] < cl && cost[k] <= cr)) continue;
-            T val = cost[k], off = T(0);
-            if (cl_ok && cr_ok) {
-                const T den = cl - T(2) * cost[k] + cr;
-                if (den > T(0)) {
-                    off = (cl - cr) / (T(2) * den);
-                    val = cost[k] - (cl - cr) * (cl - cr) / (T(8) * den);
-                }
-            }
-            if (val < best) {
-                best = val;
-                bpos = T(pidx[k]) + off;
-            }
-        }
+        if (nv == 0) break;
+        consider(c1, nv >= 2 && p1 == p2 - 1, c2, p2, alf_inf<T>(), false);
         const T nxp = bxn + bpos * stx, nyp = byn + bpos * sty;
         dx = nxp - bx;
         dy = nyp - by;
@@ -214,7 +230,6 @@ __global__ void ray_kernel(RayLaunch a)
             const T ddx = x1 - x0, ddy = y1 - y0;
             const T len = sqrt_(ddx * ddx + ddy * ddy);
             if (len == T(0)) continue;
-            const double dir = atan2((double)ddy, (double)ddx);
             // crossings of x = k + 1/2 and y = k + 1/2 strictly inside the segment, merged in order
             const bool xinc = ddx > T(0), yinc = ddy > T(0);
             T kx = xinc ? floor(x0 - T(0.5)) + T(1.5) : ceil(x0 - T(0.5)) - T(0.5);
@@ -230,7 +245,7 @@ __global__ void ray_kernel(RayLaunch a)
                 if (tn > tprev) {
                     const T tm = T(0.5) * (tprev + tn);
                     const int n = node_at(c, x0 + tm * ddx, y0 + tm * ddy);
-                    total += piece_time(c, n, (tn - tprev) * len, dir);
+                    total += piece_time(c, n, (tn - tprev) * len, ddx, ddy);
                     tprev = tn;
                 }
                 if (last) break;
