@@ -40,6 +40,10 @@ WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 
             "step = solve + FP64 check + 32 rays/source + adjoint gradient")
 # algorithmic FP32-pipe operations of one evaluation of the local operator (derivation in the design doc)
 OPS_PER_EVAL = 627.0
+# DRAM bytes (read + write) per evaluation of the field-resident sweep kernel, from an ncu capture of
+# a 2,560-field solve (profiles/fim_warp_kernel_weld_batch_80x32.md); scaled to a launch by its
+# evaluations.  Set to None when that kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": (2.401563e9 + 3.316605e9) / 332120202}
 SMS, FP32_LANES = 152, 128
 
 
@@ -197,7 +201,9 @@ def profile_run(args, wl, api, local):
             P.trace_rays(th, times)
             P.backward(th, times, rec, 2.0 * rect)
     torch.cuda.synchronize()
+    st = P.stats()
     print(json.dumps({"profile_run": True, "fields": P.nfields, "nodes": P.total_nodes, "status": P.status(),
+                      "evaluations_last_solve": st["evaluations"], "rounds_last_solve": st["rounds"],
                       "sweep": P.options.sweep, "stages": args.profile_stages,
                       "seconds": time.perf_counter() - t0}), flush=True)
 
@@ -297,6 +303,7 @@ def main():
     achieved = OPS_PER_EVAL * evals / (ev_ms * 1e-3) / 1e12
     peak = SMS * FP32_LANES * clock * 1e6 / 1e12
     evals_per_node = evals / (args.steps * P.total_nodes)
+    kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel"}[P.options.sweep]
     del Pt, tt
 
     # ---- end to end through the public API: orientations from pinned host memory, receiver times back
@@ -328,9 +335,10 @@ def main():
                 "h2d_bytes_per_step": int(th_host.numel() * th_host.element_size()),
                 "d2h_bytes_per_step": int(rt_host.numel() * rt_host.element_size()
                                           + g_host.numel() * g_host.element_size())},
-        "roofline": {"bound": "alu", "kernel": "fim_warp_kernel" if P.options.sweep == 2 else "fim_eval_kernel",
-                     "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC_BYTES_PER_EVAL[kname] * evals / args.steps / max(eval_launches // args.steps, 1)
+                                 if TRAFFIC_BYTES_PER_EVAL.get(kname) else None),
                      "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {clock:.0f} MHz (sampled clock); "
                                     f"{OPS_PER_EVAL:.0f} FP32 ops per evaluation",
                      "avg_launch_ms": ev_ms / max(eval_launches, 1), "launches": eval_launches // args.steps},
