@@ -117,7 +117,7 @@ typedef struct {
     int ctas_per_sm;        /* reserved (0) */
     int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
     double band_cells;      /* sweep schedule: nodes later than the front by more than this many
-                               cell-crossing times wait for the front (default 4; <= 0: no band) */
+                               cell-crossing times wait for the front (default 2; <= 0: no band) */
     int use_graph;          /* 1: replay the sweep rounds from a CUDA graph (default 1) */
     int time_kernels;       /* 1: time the evaluation kernel with CUDA events (alf_plan_stats; default 0) */
 } alf_options;

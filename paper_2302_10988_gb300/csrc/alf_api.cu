@@ -177,7 +177,7 @@ void alf_default_options(alf_options* o)
     o->sweep = 0;
     o->ctas_per_sm = 0;
     o->keep_records = 0;
-    o->band_cells = 4.0;
+    o->band_cells = 2.0;
     o->use_graph = 1;
     o->time_kernels = 0;
 }

@@ -764,7 +764,15 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
             tC = m1 ? t[pq(p)] : t[pp(p)];
             r = 2 * p + (m1 ? 0 : 1);
         }
-    const double v = stencil_time<double>(xA, yA, xB, yB, xC, yC, (double)tA, (double)tB, (double)tC, R);
+    // the stencil time with its geometry scaled by den = tau_C - tau_A (> 0 for a feasible pair): the
+    // cross product scales by den and the phase term by den^2, so tau_D needs no division, and one
+    // reciprocal square root instead of a square root and two divisions.  The differences of FP32
+    // times are exact in FP64.
+    const double num = (double)tB - (double)tA, den = (double)tC - (double)tA;
+    const double Ex = xA * den + num * (xC - xA), Ey = yA * den + num * (yC - yA);
+    const double ux = xB * den - Ex, uy = yB * den - Ey;
+    const double cross = fabs(yB * Ex - xB * Ey);
+    const double v = (double)tB + R.h * cross * rsqrt(phase_L<double>(R, ux, uy));
     rec = r;
     return v > (double)tC ? v : alf_inf<double>();
 }
