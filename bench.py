@@ -220,7 +220,13 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     import __graft_entry__
-    __graft_entry__.build()
+    # one build per node: local rank 0 compiles, the others load what it built
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    if local != 0:
+        __graft_entry__.build()
     from paper_2302_10988_gb300 import api, workloads as W
 
     wl = rank_workload(W, args.samples, rank)
