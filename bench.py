@@ -5,9 +5,10 @@ Workload (N = 1): the batched weld workload -- 512 media samples (region
 orientations drawn per sample) x 32 sources, grid sizes uniform in 128..320
 (step 32), 10 x 10 weld regions, FP32.  One step is one pass of the whole hot
 path over the batch: per-region constants, near-source initialisation, the
-sweep to the fixed point (rounds replayed from a CUDA graph), receiver times,
+sweep to the fixed point (the schedule the autotuner picks), receiver times,
 the FP64 convergence check, rays for 32 receivers per source and the adjoint
-gradient of a receiver-time misfit with respect to the region orientations.
+gradient of a receiver-time misfit with respect to the region orientations (the
+last three, independent of one another, on three streams after the solve).
 
 Metric: travel-time nodes/s = sum over fields of nx * ny / step time.  Also
 reported: the plain single-medium form (256 x 256, 32 sources, FP32 and FP64)
@@ -244,22 +245,39 @@ def main():
     t_obs = (t_obs + 1e-8 * torch.randn_like(t_obs)).contiguous()
 
     stage = {}
+    side = [torch.cuda.Stream(), torch.cuda.Stream()]
 
     def step(theta, timed_stages=False):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if timed_stages else None
-        if ev: ev[0].record(stream)
+        if not timed_stages:
+            # after the solve, the FP64 check (FP64 pipe), the rays (FP32) and the adjoint (memory) are
+            # independent: they run on three streams and the step ends when all three have
+            P.solve(theta, times=times, rec_times=rect, records=rec)
+            solved = torch.cuda.Event()
+            solved.record(stream)
+            for s in side:
+                s.wait_event(solved)
+            with torch.cuda.stream(side[0]):
+                mr, fl = P.check64(theta, times, rec)
+            with torch.cuda.stream(side[1]):
+                P.trace_rays(theta, times)
+            g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
+            for s in side:
+                stream.wait_stream(s)
+            return mr, fl, g
+        # stage timing: the same calls one after the other on one stream
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
         P.solve(theta, times=times, rec_times=rect, records=rec)
-        if ev: ev[1].record(stream)
+        ev[1].record(stream)
         mr, fl = P.check64(theta, times, rec)
-        if ev: ev[2].record(stream)
+        ev[2].record(stream)
         P.trace_rays(theta, times)
-        if ev: ev[3].record(stream)
+        ev[3].record(stream)
         g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
-        if ev:
-            ev[4].record(stream)
-            torch.cuda.synchronize()
-            for k, name in enumerate(["solve", "check64", "rays", "adjoint"]):
-                stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for k, name in enumerate(["solve", "check64", "rays", "adjoint"]):
+            stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
         return mr, fl, g
 
     for _ in range(max(args.warmup, 3)):

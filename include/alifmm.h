@@ -193,6 +193,11 @@ alf_status alf_plan_options(const alf_plan* plan, alf_options* out);
 alf_status alf_solve(alf_plan* plan, const double* region_theta, void* times, void* rec_times, uint8_t* records,
                      void* stream);
 
+/* After alf_solve, the three calls below read its outputs and write disjoint
+ * workspaces of the plan, so they may run at the same time on different
+ * streams (each ordered after the solve by the caller).  Two calls of the same
+ * function on one plan must not overlap. */
+
 /* FP64 convergence check (the precision policy's final check): evaluates the
  * local update F in double precision at every node of a solved field and
  * writes per field the largest |F64(tau) - tau| / tau and the number of nodes

@@ -257,6 +257,7 @@ static void plan_free(alf_plan* p)
     dfree(p->d_h);
     dfree(p->d_rec);
     dfree(p->d_regions);
+    dfree(p->d_regions_rays);
     dfree(p->d_regions64);
     dfree(p->d_q);
     dfree(p->d_ray_error);
@@ -503,6 +504,9 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         p->d_regions = r1;
         ALLOC(r2, (size_t)p->B * p->R * sizeof(RegionP<double>));
         p->d_regions64 = r2;
+        char* r3 = nullptr;
+        ALLOC(r3, (size_t)p->B * p->R * rsz);
+        p->d_regions_rays = r3;
     }
 #undef ALLOC
     if (cudaMallocHost((void**)&p->h_q, sizeof(QueueState)) != cudaSuccess ||
@@ -696,8 +700,9 @@ alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, v
     if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_trace_rays: plan has no receivers");
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);
+    // rays keep their own region constants, so that they can run beside alf_check64 and alf_backward
     ALF_CUDA(ctx, launch_prep_regions(p->opt.precision, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
-                                      p->opt.group_model, p->d_regions, st));
+                                      p->opt.group_model, p->d_regions_rays, st));
     RayLaunch a;
     a.times = times;
     a.fields = p->d_fields;
@@ -705,7 +710,7 @@ alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, v
     a.region_map = p->d_map;
     a.region_mat = p->d_region_mat;
     a.mats = p->d_mats;
-    a.regions = p->d_regions;
+    a.regions = p->d_regions_rays;
     a.theta = theta;
     a.nregions = p->R;
     a.rec_ij = p->d_rec;

@@ -213,6 +213,7 @@ struct alf_plan {
     int32_t* d_rec = nullptr;
     void* d_regions = nullptr;    // RegionP<T> of the plan precision
     void* d_regions64 = nullptr;  // RegionP<double> for the FP64 check
+    void* d_regions_rays = nullptr;  // RegionP<T> of the ray tracer (its own copy: rays may overlap the others)
     // sweep workspace
     unsigned* d_list0 = nullptr;
     unsigned* d_list1 = nullptr;
