@@ -9,6 +9,10 @@
 
 #include "alf_internal.h"
 
+// CTAs per SM of the FP64 check: enough warps for the FP64 pipe, room left for other streams'
+// kernels (rays, adjoint) on the same SMs
+#define ALF_CHECK_CTAS_PER_SM 2
+
 using namespace alf;
 
 namespace {
@@ -686,7 +690,7 @@ alf_status alf_check64(alf_plan* p, const double* theta, const void* times, cons
     ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
                                       p->opt.group_model, p->d_regions64, st));
     ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
-                                 records, p->d_frozen, p->box, max_rel, n_flips, st));
+                                 records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st));
     return ALF_OK;
 }
 

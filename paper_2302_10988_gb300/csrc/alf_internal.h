@@ -90,7 +90,8 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
                             cudaStream_t st);
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
                            const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
-                           const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, cudaStream_t st);
+                           const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
+                           cudaStream_t st);
 cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
                                  double* out, int n, cudaStream_t st);
 

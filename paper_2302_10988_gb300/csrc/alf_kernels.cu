@@ -9,6 +9,7 @@
 //  fim_warp       the same sweep with one warp per field, the whole solve in one launch
 //  finalize       clears the frozen marks and gathers receiver times
 //  check64        FP64 evaluation of F at every node of a solved field
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -778,21 +779,25 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
 }
 
 template <typename T>
-__global__ void check64_kernel(const T* times, const FieldDesc* fields, const uint16_t* region_map,
+__global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint16_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
                                const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips)
 {
-    const int f = blockIdx.y;
+    // persistent: the CTAs stride over (field, chunk) work items, so that a small grid leaves room on
+    // the SMs for kernels of other streams while this one keeps the FP64 pipe busy
+    constexpr int CH = 32;  // chunks per field
+    __shared__ float s_max[256];
+    __shared__ int s_flip[256];
+    const double inf64 = alf_inf<double>();
+    for (long long w = blockIdx.x; w < (long long)nfields * CH; w += gridDim.x) {
+    const int f = (int)(w / CH), chunk = (int)(w % CH);
     const FieldDesc fd = fields[f];
     const unsigned* fb = frozen_bits + (size_t)f * frozen_words(box);
     const int n = fd.nx * fd.ny;
-    __shared__ float s_max[256];
-    __shared__ int s_flip[256];
     float mx = 0.f;
     int flips = 0;
     const T* tf = times + fd.node_off;
-    const double inf64 = alf_inf<double>();
-    for (int me = blockIdx.x * blockDim.x + threadIdx.x; me < n; me += gridDim.x * blockDim.x) {
+    for (int me = chunk * blockDim.x + threadIdx.x; me < n; me += CH * blockDim.x) {
         const int i = me % fd.nx, j = me / fd.nx;
         if (box_frozen(fb, box, fd, i, j)) continue;
         const T tme = abs_(tf[me]);
@@ -912,26 +917,30 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, const ui
     }
     if (threadIdx.x == 0) {
         // max of non-negative doubles through their bit patterns
-        atomicMax((unsigned long long*)(max_rel + f), (unsigned long long)__double_as_longlong((double)s_max[0]));
-        atomicAdd(n_flips + f, s_flip[0]);
+        if (s_max[0] > 0.f)
+            atomicMax((unsigned long long*)(max_rel + f), (unsigned long long)__double_as_longlong((double)s_max[0]));
+        if (s_flip[0]) atomicAdd(n_flips + f, s_flip[0]);
+    }
+    __syncthreads();
     }
 }
 
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
                            const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
-                           const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, cudaStream_t st)
+                           const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
+                           cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(max_rel, 0, sizeof(double) * nfields, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(n_flips, 0, sizeof(int32_t) * nfields, st);
     if (e != cudaSuccess) return e;
-    dim3 grid(32, nfields);
+    const int grid = std::max(1, grid_ctas);
     if (precision == ALF_FP64)
-        check64_kernel<double><<<grid, 256, 0, st>>>((const double*)times, fields, region_map,
+        check64_kernel<double><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map,
                                                      (const RegionP<double>*)regions64, nregions, records,
                                                      frozen_bits, box, max_rel, n_flips);
     else
-        check64_kernel<float><<<grid, 256, 0, st>>>((const float*)times, fields, region_map,
+        check64_kernel<float><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map,
                                                     (const RegionP<double>*)regions64, nregions, records,
                                                     frozen_bits, box, max_rel, n_flips);
     note_launches(1);
