@@ -694,6 +694,7 @@ typedef struct {
     int halfwidth;
     double stop_radius;
     int max_pts;
+    int family; /* -1: the family most perpendicular to the ray at every step; 0..3: one fixed family */
 } om_ray_opts;
 
 /* families: 0 vertical x=c, 1 horizontal y=c, 2 diagonal x-y=c, 3 diagonal x+y=c */
@@ -735,22 +736,28 @@ int om_trace_ray(const om_medium* M, const double* tau, double x0, double y0, do
             status = 0;
             break;
         }
-        /* plane family most perpendicular to the current direction */
+        /* plane family most perpendicular to the current direction, or the fixed one (Sec. 5.1 uses
+           each of the four sets on its own, and changes set along the ray) */
         double dl = sqrt(dx * dx + dy * dy);
         int fam = 0;
-        double bestc = -1.0;
-        for (int f = 0; f < 4; ++f) {
-            double nl = sqrt(FAM_N[f][0] * FAM_N[f][0] + FAM_N[f][1] * FAM_N[f][1]);
-            double c = fabs(dx * FAM_N[f][0] + dy * FAM_N[f][1]) / (dl * nl);
-            if (c > bestc + 1e-12) {
-                bestc = c;
-                fam = f;
+        if (o->family >= 0) {
+            fam = o->family;
+        } else {
+            double bestc = -1.0;
+            for (int f = 0; f < 4; ++f) {
+                double nl = sqrt(FAM_N[f][0] * FAM_N[f][0] + FAM_N[f][1] * FAM_N[f][1]);
+                double c = fabs(dx * FAM_N[f][0] + dy * FAM_N[f][1]) / (dl * nl);
+                if (c > bestc + 1e-12) {
+                    bestc = c;
+                    fam = f;
+                }
             }
         }
         double nxf = FAM_N[fam][0], nyf = FAM_N[fam][1];
         double qB = nxf * bx + nyf * by;
         double qT = nxf * xt + nyf * yt;
-        double sg = (dx * nxf + dy * nyf) >= 0.0 ? 1.0 : -1.0;
+        /* a fixed family crosses its planes towards the target, each plane once */
+        double sg = o->family >= 0 ? (qT - qB >= 0.0 ? 1.0 : -1.0) : ((dx * nxf + dy * nyf) >= 0.0 ? 1.0 : -1.0);
         double scale = sqrt(nxf * nxf + nyf * nyf); /* q units per cell of normal distance */
         double qn = floor(qB + sg * o->plane_step * scale + 0.5);
         /* [R12] never place the plane beyond the target */

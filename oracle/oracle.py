@@ -49,7 +49,7 @@ class Medium(C.Structure):
 
 class RayOpts(C.Structure):
     _fields_ = [("plane_step", C.c_int), ("halfwidth", C.c_int), ("stop_radius", C.c_double),
-                ("max_pts", C.c_int)]
+                ("max_pts", C.c_int), ("family", C.c_int)]
 
 
 def lib():
@@ -231,14 +231,16 @@ def solve_field(M: OMedium, si, sj, r0=2):
     return tau, rec, stats, frozen.reshape(M.ny, M.nx)
 
 
-def trace_ray(M: OMedium, tau, start, target, plane_step=4, halfwidth=8, stop_radius=1.6, max_pts=None):
-    """Fermat plane-walk ray from `start` to `target` (the source of `tau`), grid units."""
+def trace_ray(M: OMedium, tau, start, target, plane_step=4, halfwidth=8, stop_radius=1.6, max_pts=None, family=-1):
+    """Fermat plane-walk ray from `start` to `target` (the source of `tau`), grid units.  family -1: the
+    plane set most perpendicular to the ray at every step; 0..3: one fixed set (x = c, y = c, x - y = c,
+    x + y = c), Sec. 5.1."""
     if max_pts is None:
         max_pts = 4 * (M.nx + M.ny) + 2
     t = np.ascontiguousarray(tau, np.float64).reshape(-1)
     pts = np.zeros(2 * max_pts, np.float64)
     n = C.c_int(0)
-    o = RayOpts(int(plane_step), int(halfwidth), float(stop_radius), int(max_pts))
+    o = RayOpts(int(plane_step), int(halfwidth), float(stop_radius), int(max_pts), int(family))
     st = lib().om_trace_ray(C.byref(M.c), _ptr(t, C.c_double), float(start[0]), float(start[1]), float(target[0]),
                             float(target[1]), C.byref(o), _ptr(pts, C.c_double), C.byref(n))
     return pts[:2 * n.value].reshape(-1, 2).copy(), st
@@ -247,6 +249,21 @@ def trace_ray(M: OMedium, tau, start, target, plane_step=4, halfwidth=8, stop_ra
 def path_time(M: OMedium, pts) -> float:
     p = np.ascontiguousarray(pts, np.float64).reshape(-1)
     return lib().om_path_time(C.byref(M.c), _ptr(p, C.c_double), int(p.size // 2))
+
+
+def trace_ray_best_family(M: OMedium, tau, start, target, **kw):
+    """The fastest of the four fixed-family rays (ties to the lower family).  Returns (pts, status, family)."""
+    best = None
+    for fam in range(4):
+        pts, st = trace_ray(M, tau, start, target, family=fam, **kw)
+        if st != 0:
+            continue
+        t = path_time(M, pts)
+        if best is None or t < best[0]:
+            best = (t, pts, st, fam)
+    if best is None:
+        return None, 1, -1
+    return best[1], best[2], best[3]
 
 
 def adjoint(M: OMedium, frozen, tau, rec, order, seeds, src, region, nregions, grad=None):

@@ -98,3 +98,53 @@ def test_homogeneous_ray_is_straight(oracle):
             straight = np.linalg.norm(b - a) * 1e-3 / oracle.group_exact(m, np.arctan2(*(b - a)[::-1]) - th)[1]
             t = oracle.path_time(M, pts)
             assert straight * (1 - 0.006) <= t <= straight * 1.01
+
+
+def _homogeneous(oracle, th=0.6, n=80):
+    c6, rho = W.WELD_TI
+    m = oracle.mat_from_voigt(c6, rho)
+    M = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m])
+    fr, t0 = oracle.init_hierarchy(M, 10, 0)
+    return M, oracle.fmm(M, fr, t0)[0], m
+
+
+def test_fixed_family_points_lie_on_its_planes(oracle):
+    """Sec. 5.1: with one fixed set of planes every interior ray point lies on a plane of that set
+    (x = c, y = c, x - y = c, x + y = c with integer c), and successive points cross successive planes."""
+    M, tau, m = _homogeneous(oracle)
+    for fam, coord in ((0, lambda p: p[:, 0]), (1, lambda p: p[:, 1]), (2, lambda p: p[:, 0] - p[:, 1]),
+                       (3, lambda p: p[:, 0] + p[:, 1])):
+        pts, st = oracle.trace_ray(M, tau, (70, 79), (10, 0), family=fam)
+        assert st == 0
+        q = coord(pts[1:-1])
+        assert np.allclose(q, np.round(q), atol=1e-9), fam
+        steps = np.diff(coord(pts[:-1]))
+        assert np.all(steps != 0) and (np.all(steps > 0) or np.all(steps < 0)), fam
+
+
+def test_fixed_family_without_planes_between_gives_two_points(oracle):
+    """Sec. 5.3: when source and receiver share the x coordinate no vertical plane lies between them, and
+    the ray of the vertical planes is just the receiver and the source."""
+    M, tau, m = _homogeneous(oracle)
+    pts, st = oracle.trace_ray(M, tau, (10, 79), (10, 0), family=0)
+    assert st == 0
+    assert pts.shape == (2, 2) and tuple(pts[0]) == (10.0, 79.0) and tuple(pts[1]) == (10.0, 0.0)
+
+
+def test_fixed_families_in_a_homogeneous_medium(oracle):
+    """Sec. 5.3: in a homogeneous medium each set of planes that separates the ends gives a near-straight
+    ray, and the best of the four is no slower than any of them."""
+    M, tau, m = _homogeneous(oracle)
+    a, b = np.array([10.0, 0.0]), np.array([70.0, 79.0])
+    u = (b - a) / np.linalg.norm(b - a)
+    times = []
+    for fam in range(4):
+        pts, st = oracle.trace_ray(M, tau, tuple(b), tuple(a), family=fam)
+        assert st == 0
+        off = np.abs((pts - a) @ np.array([-u[1], u[0]]))
+        assert off.max() < 3.0, (fam, off.max())  # within one plane spacing (4 cells) of the segment
+        times.append(oracle.path_time(M, pts))
+    straight = np.linalg.norm(b - a) * 1e-3 / oracle.group_exact(m, np.arctan2(*(b - a)[::-1]) - 0.6)[1]
+    assert min(times) >= straight * (1 - 0.006) and max(times) <= straight * 1.02
+    pts, st, fam = oracle.trace_ray_best_family(M, tau, tuple(b), tuple(a))
+    assert st == 0 and oracle.path_time(M, pts) == min(times) and fam == int(np.argmin(times))
