@@ -114,7 +114,9 @@ typedef struct {
                                shared memory per warp, nx*ny <= 2^18); 3 = one CTA owns each field,
                                one launch (suits few large fields); 0 = choose (2 when it fits and the
                                fields fill the GPU, else 3), default 0 */
-    int ctas_per_sm;        /* reserved (0) */
+    int ray_family;         /* planes of the ray tracer (Sec. 5.1): 0 = the set most perpendicular to the
+                               ray at every step (default); 1..4 = one fixed set: x = c, y = c, x - y = c,
+                               x + y = c; 5 = the fastest of the four fixed sets (Table 3 compares them) */
     int keep_records;       /* 1: keep per-node stencil records for alf_backward (default 0) */
     double band_cells;      /* sweep schedule: nodes later than the front by more than this many
                                cell-crossing times wait for the front (default 2; <= 0: no band) */

@@ -44,7 +44,7 @@ class alf_options(C.Structure):
                 ("n_levels", C.c_int), ("level_density", C.c_int * 4), ("level_radius", C.c_int * 4),
                 ("plane_step", C.c_int), ("ray_halfwidth", C.c_int), ("stop_radius", C.c_double),
                 ("max_ray_points", C.c_int), ("max_rounds", C.c_int), ("sweep", C.c_int),
-                ("ctas_per_sm", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double),
+                ("ray_family", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double),
                 ("use_graph", C.c_int), ("time_kernels", C.c_int)]
 
 

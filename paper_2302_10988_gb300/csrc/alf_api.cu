@@ -179,7 +179,7 @@ void alf_default_options(alf_options* o)
     o->max_ray_points = 512;
     o->max_rounds = 64;
     o->sweep = 0;
-    o->ctas_per_sm = 0;
+    o->ray_family = 0;
     o->keep_records = 0;
     o->band_cells = 2.0;
     o->use_graph = 1;
@@ -300,7 +300,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
     }
     if (opt.sweep < 0 || opt.sweep > 3) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1, 2 or 3");
-    if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 64) return fail(ctx, ALF_ERR_INVALID_ARG, "ctas_per_sm out of range");
+    if (opt.ray_family < 0 || opt.ray_family > 5) return fail(ctx, ALF_ERR_INVALID_ARG, "ray_family must be in 0..5");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
@@ -722,6 +722,7 @@ alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, v
     a.nrec = p->Rr;
     a.group_model = p->opt.group_model;
     a.plane_step = p->opt.plane_step;
+    a.family = p->opt.ray_family - 1;
     a.halfwidth = p->opt.ray_halfwidth;
     a.max_pts = p->opt.max_ray_points;
     a.stop_radius = p->opt.stop_radius;

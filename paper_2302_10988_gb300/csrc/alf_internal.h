@@ -173,6 +173,7 @@ struct RayLaunch {
     int nsrc, nrec;
     int group_model;
     int plane_step, halfwidth, max_pts;
+    int family;  // -1: the plane set most perpendicular at every step; 0..3: one fixed set; 4: fastest of the four
     double stop_radius;
     void* pts;
     int32_t* npts;

@@ -104,13 +104,17 @@ __global__ void ray_kernel(RayLaunch a)
     T* pts = (T*)a.pts + (size_t)ray * a.max_pts * 2;
 
     const T xt = T(fd.si), yt = T(fd.sj);
-    T bx = T(a.rec_ij[((size_t)b * a.nrec + r) * 2]), by = T(a.rec_ij[((size_t)b * a.nrec + r) * 2 + 1]);
+    const T x0r = T(a.rec_ij[((size_t)b * a.nrec + r) * 2]), y0r = T(a.rec_ij[((size_t)b * a.nrec + r) * 2 + 1]);
+    // one plane walk from the receiver to the source; famsel -1: the set most perpendicular to the ray at
+    // every step, 0..3: one fixed set (Sec. 5.1).  Returns the point count.
+    auto walk = [&](int famsel, int& status) -> int {
+    T bx = x0r, by = y0r;
     T dx = xt - bx, dy = yt - by;
     int np = 0;
     pts[0] = bx;
     pts[1] = by;
     np = 1;
-    int status = 1;
+    status = 1;
     while (np < a.max_pts) {
         const T rx = xt - bx, ry = yt - by;
         if (sqrt_(rx * rx + ry * ry) < T(a.stop_radius)) {
@@ -121,21 +125,25 @@ __global__ void ray_kernel(RayLaunch a)
             break;
         }
         const T dl = sqrt_(dx * dx + dy * dy);
-        int fam = 0;
-        T bestc = T(-1);
+        int fam = famsel;
+        if (famsel < 0) {
+            fam = 0;
+            T bestc = T(-1);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const T nl = sqrt_(T(fam_nx(k) * fam_nx(k) + fam_ny(k) * fam_ny(k)));
-            const T cs = abs_(dx * T(fam_nx(k)) + dy * T(fam_ny(k))) / (dl * nl);
-            if (cs > bestc + T(1e-12)) {
-                bestc = cs;
-                fam = k;
+            for (int k = 0; k < 4; ++k) {
+                const T nl = sqrt_(T(fam_nx(k) * fam_nx(k) + fam_ny(k) * fam_ny(k)));
+                const T cs = abs_(dx * T(fam_nx(k)) + dy * T(fam_ny(k))) / (dl * nl);
+                if (cs > bestc + T(1e-12)) {
+                    bestc = cs;
+                    fam = k;
+                }
             }
         }
         const T nxf = T(fam_nx(fam)), nyf = T(fam_ny(fam));
         const T qB = nxf * bx + nyf * by, qT = nxf * xt + nyf * yt;
         const T dn = dx * nxf + dy * nyf;
-        const T sg = dn >= T(0) ? T(1) : T(-1);
+        // a fixed set crosses its planes towards the target, each plane once
+        const T sg = famsel >= 0 ? (qT - qB >= T(0) ? T(1) : T(-1)) : (dn >= T(0) ? T(1) : T(-1));
         const T scale = sqrt_(nxf * nxf + nyf * nyf);
         T qn = floor(qB + sg * T(a.plane_step) * scale + T(0.5));
         if (sg * (qn - qT) > T(0)) qn = floor(qT + T(0.5));
@@ -220,10 +228,10 @@ __global__ void ray_kernel(RayLaunch a)
         pts[2 * np + 1] = by;
         np++;
     }
-    a.npts[ray] = np;
-    if (a.ray_status) a.ray_status[ray] = status;
-    if (status != 0) atomicCAS(a.error, 0u, (unsigned)ALF_ERR_RAY_INCOMPLETE);
-    if (a.ray_time) {
+        return np;
+    };
+    // time along the polyline through the nearest-node cells
+    auto path_time = [&](int np) -> T {
         T total = T(0);
         for (int s = 0; s + 1 < np; ++s) {
             const T x0 = pts[2 * s], y0 = pts[2 * s + 1], x1 = pts[2 * s + 2], y1 = pts[2 * s + 3];
@@ -253,8 +261,39 @@ __global__ void ray_kernel(RayLaunch a)
                 if (ty <= tx) ky += yinc ? T(1) : T(-1);
             }
         }
-        ((T*)a.ray_time)[ray] = total;
+        return total;
+    };
+    int status = 1, np = 0;
+    T total = T(0);
+    if (a.family == 4) {
+        // the fastest of the four fixed sets (ties to the lower set), traced again to leave its points
+        T best = alf_inf<T>();
+        int bestf = -1;
+        for (int fam = 0; fam < 4; ++fam) {
+            int st = 1;
+            const int n = walk(fam, st);
+            if (st != 0) continue;
+            const T tt = path_time(n);
+            if (tt < best) {
+                best = tt;
+                bestf = fam;
+            }
+        }
+        if (bestf < 0) {
+            np = walk(0, status);
+            if (a.ray_time) total = path_time(np);
+        } else {
+            np = walk(bestf, status);
+            total = best;
+        }
+    } else {
+        np = walk(a.family, status);
+        if (a.ray_time) total = path_time(np);
     }
+    a.npts[ray] = np;
+    if (a.ray_status) a.ray_status[ray] = status;
+    if (status != 0) atomicCAS(a.error, 0u, (unsigned)ALF_ERR_RAY_INCOMPLETE);
+    if (a.ray_time) ((T*)a.ray_time)[ray] = total;
 }
 
 cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st)

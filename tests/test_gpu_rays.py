@@ -68,3 +68,42 @@ def test_velocity_gradient_ray_gpu(api):
     cx, cy, R = 1 - v0 / g, 30 + v0 * cot / g, v0 * np.sqrt(1 + cot * cot) / g
     assert np.abs(np.hypot(p[:, 0] - cx, p[:, 1] - cy) - R).max() < 1.0
     assert float(rtime[0, 0, 0]) == pytest.approx(5.0884053e-05, rel=5e-4)
+
+
+@pytest.mark.parametrize("ray_family", [1, 2, 3, 4, 5])
+def test_ray_families_fp64_match_oracle(api, oracle, ray_family):
+    """Rays on one fixed set of planes (1..4) and the fastest of the four (5), Sec. 5.1 and Table 3: same
+    points and times as the oracle's tracer on the oracle's field."""
+    wl = W.homogeneous_ti()
+    P = api.Plan(wl, precision="fp64", ray_family=ray_family)
+    th = P.theta_tensor()
+    times, rt = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    assert P.status() == 0
+    tau, orec, fr, M = oracle_field(oracle, wl, 0, 0)
+    src = wl.samples[0].src[0]
+    for r, rec in enumerate(wl.samples[0].rec):
+        if ray_family == 5:
+            opts, ost, fam = oracle.trace_ray_best_family(M, tau, rec, src)
+        else:
+            opts, ost = oracle.trace_ray(M, tau, rec, src, family=ray_family - 1)
+        n = int(npts[0, 0, r])
+        assert ost == 0 and int(st[0, 0, r]) == 0
+        assert n == len(opts), (r, n, len(opts))
+        assert np.abs(pts[0, 0, r, :n].cpu().numpy() - opts).max() < 1e-7
+        assert float(rtime[0, 0, r]) == pytest.approx(oracle.path_time(M, opts), rel=1e-10)
+
+
+def test_best_family_is_fastest_fp32_weld(api):
+    """The fastest-of-four rays are never slower than any single fixed set, ray by ray."""
+    wl = W.weld_single(n=96, h=0.5e-3, rg=6, seed=7, nsrc=3, nrec=8)
+    out = {}
+    for fam in (1, 2, 3, 4, 5):
+        P = api.Plan(wl, precision="fp32", ray_family=fam)
+        th = P.theta_tensor()
+        times, _ = P.solve(th)
+        pts, npts, rtime, st = P.trace_rays(th, times)
+        assert int((st != 0).sum()) == 0
+        out[fam] = rtime.cpu().numpy()
+    best = np.minimum.reduce([out[f] for f in (1, 2, 3, 4)])
+    assert np.array_equal(out[5], best)
