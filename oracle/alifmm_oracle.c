@@ -782,6 +782,19 @@ int om_trace_ray(const om_medium* M, const double* tau, double x0, double y0, do
         double tx = FAM_T[fam][0], ty = FAM_T[fam][1];
         double pc = (fam == 0) ? py : px; /* for families 1-3 the x coordinate is the parameter */
         int p0 = (int)floor(pc + 0.5);
+        /* [R18] the window is centred on the part of the plane inside the grid: a set of planes nearly
+           parallel to the ray meets the ray's line far off the grid */
+        {
+            int qi = (int)qn, lo, hi;
+            if (fam == 0) { lo = 0; hi = M->ny - 1; }
+            else if (fam == 1) { lo = 0; hi = M->nx - 1; }
+            else if (fam == 2) { lo = qi > 0 ? qi : 0; hi = M->nx - 1 < M->ny - 1 + qi ? M->nx - 1 : M->ny - 1 + qi; }
+            else { lo = qi - (M->ny - 1) > 0 ? qi - (M->ny - 1) : 0; hi = M->nx - 1 < qi ? M->nx - 1 : qi; }
+            if (lo <= hi) {
+                if (p0 < lo) p0 = lo;
+                if (p0 > hi) p0 = hi;
+            }
+        }
         int plo = p0 - o->halfwidth, phi = p0 + o->halfwidth;
         /* clip to nodes inside the grid */
         double cost[64];

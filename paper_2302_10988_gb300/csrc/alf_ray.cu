@@ -172,7 +172,27 @@ __global__ void ray_kernel(RayLaunch a)
         }
         const T stx = T(fam_tx(fam)), sty = T(fam_ty(fam));
         const T pc = fam == 0 ? py : px;
-        const int p0 = (int)floor((double)pc + 0.5);
+        int p0 = (int)floor((double)pc + 0.5);
+        {
+            // the window is centred on the part of the plane inside the grid (a set of planes nearly
+            // parallel to the ray meets the ray's line far off the grid)
+            const int qi = (int)qn;
+            int lo, hi;
+            if (fam == 0) {
+                lo = 0;
+                hi = fd.ny - 1;
+            } else if (fam == 1) {
+                lo = 0;
+                hi = fd.nx - 1;
+            } else if (fam == 2) {
+                lo = max(qi, 0);
+                hi = min(fd.nx - 1, fd.ny - 1 + qi);
+            } else {
+                lo = max(qi - (fd.ny - 1), 0);
+                hi = min(fd.nx - 1, qi);
+            }
+            if (lo <= hi) p0 = min(max(p0, lo), hi);
+        }
         // candidates streamed in order of p: every local minimum (with its neighbours when they are
         // consecutive candidates) is refined by a parabola as soon as its right neighbour is known
         T best = alf_inf<T>();
