@@ -251,6 +251,22 @@ def path_time(M: OMedium, pts) -> float:
     return lib().om_path_time(C.byref(M.c), _ptr(p, C.c_double), int(p.size // 2))
 
 
+def ray_gradient(M: OMedium, pts, region_of_node, nregions, eps=1e-6):
+    """Gradient of the time along the fixed path `pts` with respect to the region orientations: for every
+    region, the central difference of the path time (Sec. 5.1 integration) with that region's orientation
+    moved by +-eps.  region_of_node: region index of every node (row-major)."""
+    reg = np.asarray(region_of_node).reshape(-1)
+    g = np.zeros(nregions)
+    for r in np.unique(reg):
+        tp, tm = M.theta.copy(), M.theta.copy()
+        tp[reg == r] += eps
+        tm[reg == r] -= eps
+        Mp = OMedium(M.nx, M.ny, M.h, M.mat_id, tp, M.mats, M.group_model)
+        Mm = OMedium(M.nx, M.ny, M.h, M.mat_id, tm, M.mats, M.group_model)
+        g[r] = (path_time(Mp, pts) - path_time(Mm, pts)) / (2 * eps)
+    return g
+
+
 def trace_ray_best_family(M: OMedium, tau, start, target, **kw):
     """The fastest of the four fixed-family rays (ties to the lower family).  Returns (pts, status, family)."""
     best = None

@@ -148,3 +148,39 @@ def test_fixed_families_in_a_homogeneous_medium(oracle):
     assert min(times) >= straight * (1 - 0.006) and max(times) <= straight * 1.02
     pts, st, fam = oracle.trace_ray_best_family(M, tau, tuple(b), tuple(a))
     assert st == 0 and oracle.path_time(M, pts) == min(times) and fam == int(np.argmin(times))
+
+
+def test_ray_gradient_closed_form(oracle):
+    """Along a fixed straight path in a homogeneous medium the time is L h / V(phi - theta), so its
+    derivative by the orientation is that closed form's, from the (pinned) exact ray velocity."""
+    n = 60
+    c6, rho = W.WELD_TI
+    m = oracle.mat_from_voigt(c6, rho)
+    th = 0.4
+    M = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m], group_model=oracle.GROUP_EXACT)
+    a, b = np.array([5.0, 3.0]), np.array([52.0, 40.0])
+    pts = np.stack([b, 0.5 * (a + b), a])
+    L = np.linalg.norm(b - a) * 1e-3
+    phi = np.arctan2(*(a - b)[::-1])
+    e = 1e-5
+    closed = (L / oracle.group_exact(m, phi - th - e)[1] - L / oracle.group_exact(m, phi - th + e)[1]) / (2 * e)
+    g = oracle.ray_gradient(M, pts, np.zeros(n * n, np.int64), 1)
+    assert g[0] == pytest.approx(closed, rel=1e-6)
+    assert oracle.path_time(M, pts) == pytest.approx(L / oracle.group_exact(m, phi - th)[1], rel=1e-12)
+
+
+def test_ray_gradient_sums_regions(oracle):
+    """Moving every region by the same angle moves the whole medium: the region derivatives of a path
+    through several regions add up to the derivative for one orientation shared by all of them."""
+    wl = W.weld_single(n=40, h=0.5e-3, rg=4, seed=5, nsrc=1, nrec=1)
+    s = wl.samples[0]
+    mats = [oracle.mat_from_voigt(c6, rho) for c6, rho in wl.materials]
+    M = oracle.OMedium.from_regions(s.nx, s.ny, s.h, s.region_map, s.region_theta, wl.region_material, mats)
+    pts = np.array([[3.0, 39.0], [15.0, 25.0], [22.0, 12.0], [30.0, 0.0]])
+    g = oracle.ray_gradient(M, pts, s.region_map.reshape(-1), wl.nregions)
+    e = 1e-6
+    Mp = oracle.OMedium(M.nx, M.ny, M.h, M.mat_id, M.theta + e, M.mats, M.group_model)
+    Mm = oracle.OMedium(M.nx, M.ny, M.h, M.mat_id, M.theta - e, M.mats, M.group_model)
+    total = (oracle.path_time(Mp, pts) - oracle.path_time(Mm, pts)) / (2 * e)
+    assert np.sum(g) == pytest.approx(total, rel=1e-5)
+    assert np.count_nonzero(g) >= 3
