@@ -225,6 +225,19 @@ alf_status alf_check64(alf_plan* plan, const double* region_theta, const void* t
 alf_status alf_trace_rays(alf_plan* plan, const double* region_theta, const void* times, void* ray_pts,
                           int32_t* ray_npts, void* ray_time, int32_t* ray_status, void* stream);
 
+/* Gradient of ray times along fixed paths (Sec. 5.1 integration; the paper's
+ * motivation for ray paths, Sec. 1, is exactly this use in inversions): with
+ * each ray's polyline held fixed, its time is the sum over pieces of
+ * len h / V(dir - theta_region), and this returns, for every region,
+ * dL/dtheta = sum over rays of dL/dT_ray * dT_ray/dtheta_region.  Cheaper than
+ * alf_backward (no sweep) and first order in the path, which is optimal.
+ *  ray_pts, ray_npts  the output of alf_trace_rays for the same plan
+ *  dL_dray      [nsamples][nsources][nreceivers], dtype of the plan, input
+ *  dL_dtheta    [nsamples][nregions] double, output (overwritten)
+ * May run beside alf_check64 and alf_backward (it writes only dL_dtheta). */
+alf_status alf_ray_gradient(alf_plan* plan, const double* region_theta, const void* ray_pts, const int32_t* ray_npts,
+                            const void* dL_dray, double* dL_dtheta, void* stream);
+
 /* Adjoint (reverse-mode) gradient of the receiver times: given dL/dT at every
  * receiver, returns dL/dtheta for every region, by differentiating the chosen
  * stencil (or fallback) of every node and the straight-ray initialisation,

@@ -155,6 +155,16 @@ class Plan:
                          C.c_void_p(st.data_ptr()), self._stream())
         return pts, npts, rt, st
 
+    def ray_gradient(self, theta, pts, npts, dL_dray):
+        """dL/dtheta [nsamples, nregions] (float64) from dL/dT of every ray, its path (from trace_rays) held
+        fixed."""
+        grad = torch.empty((self.nsamples, self.nregions), dtype=torch.float64, device=self._dev())
+        g = dL_dray.to(self.dtype).contiguous()
+        B.alf_ray_gradient(self.ctx, self.plan, C.c_void_p(theta.data_ptr()), C.c_void_p(pts.data_ptr()),
+                           C.c_void_p(npts.data_ptr()), C.c_void_p(g.data_ptr()), C.c_void_p(grad.data_ptr()),
+                           self._stream())
+        return grad
+
     def backward(self, theta, times, records, dL_drec):
         """dL/dtheta [nsamples, nregions] (float64) from dL/dT at the receivers (plan needs keep_records=1)."""
         grad = torch.empty((self.nsamples, self.nregions), dtype=torch.float64, device=self._dev())

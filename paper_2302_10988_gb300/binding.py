@@ -26,7 +26,7 @@ ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
 EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error", "alf_plan_create",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
            "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats", "alf_plan_autotune",
-           "alf_eval_velocity", "alf_solve_field_noalloc")
+           "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient")
 
 
 class AlfError(RuntimeError):
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
         L.alf_check64.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.alf_trace_rays.restype = C.c_int
         L.alf_trace_rays.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.alf_ray_gradient.restype = C.c_int
+        L.alf_ray_gradient.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.alf_backward.restype = C.c_int
         L.alf_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.alf_sync_status.restype = C.c_int
@@ -181,6 +183,10 @@ def alf_check64(ctx, plan, theta_ptr, times_ptr, records_ptr, max_rel_ptr, flips
 
 def alf_trace_rays(ctx, plan, theta_ptr, times_ptr, pts_ptr, npts_ptr, time_ptr, status_ptr, stream):
     _check(ctx, load().alf_trace_rays(plan, theta_ptr, times_ptr, pts_ptr, npts_ptr, time_ptr, status_ptr, stream))
+
+
+def alf_ray_gradient(ctx, plan, theta_ptr, pts_ptr, npts_ptr, dray_ptr, grad_ptr, stream):
+    _check(ctx, load().alf_ray_gradient(plan, theta_ptr, pts_ptr, npts_ptr, dray_ptr, grad_ptr, stream))
 
 
 def alf_backward(ctx, plan, theta_ptr, times_ptr, records_ptr, dl_ptr, grad_ptr, stream):

@@ -731,7 +731,37 @@ alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, v
     a.ray_time = ray_time;
     a.ray_status = ray_status;
     a.error = p->d_ray_error;
+    a.h_of_sample = p->d_h;
     ALF_CUDA(ctx, launch_rays(p->opt.precision, a, st));
+    return ALF_OK;
+}
+
+alf_status alf_ray_gradient(alf_plan* p, const double* theta, const void* ray_pts, const int32_t* ray_npts,
+                            const void* dL_dray, double* dL_dtheta, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !ray_pts || !ray_npts || !dL_dray || !dL_dtheta)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_ray_gradient: null pointer");
+    if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_ray_gradient: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    RayLaunch a{};
+    a.fields = p->d_fields;
+    a.nfields = p->nfields;
+    a.region_map = p->d_map;
+    a.region_mat = p->d_region_mat;
+    a.mats = p->d_mats;
+    a.theta = theta;
+    a.nregions = p->R;
+    a.nsrc = p->S;
+    a.nrec = p->Rr;
+    a.group_model = p->opt.group_model;
+    a.max_pts = p->opt.max_ray_points;
+    a.pts = const_cast<void*>(ray_pts);
+    a.npts = const_cast<int32_t*>(ray_npts);
+    a.h_of_sample = p->d_h;
+    ALF_CUDA(ctx, launch_ray_gradient(p->opt.precision, a, dL_dray, dL_dtheta, p->B, st));
     return ALF_OK;
 }
 

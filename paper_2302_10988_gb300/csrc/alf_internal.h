@@ -174,6 +174,7 @@ struct RayLaunch {
     int group_model;
     int plane_step, halfwidth, max_pts;
     int family;  // -1: the plane set most perpendicular at every step; 0..3: one fixed set; 4: fastest of the four
+    const double* h_of_sample;  // grid spacing of every sample (device)
     double stop_radius;
     void* pts;
     int32_t* npts;
@@ -182,6 +183,9 @@ struct RayLaunch {
     unsigned* error;
 };
 cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st);
+// gradient of the ray times along the given paths (a.pts, a.npts) by the region orientations
+cudaError_t launch_ray_gradient(int precision, const RayLaunch& a, const void* dL_dray, double* grad, int nsamples,
+                                cudaStream_t st);
 
 }  // namespace alf
 

@@ -316,6 +316,94 @@ __global__ void ray_kernel(RayLaunch a)
     if (a.ray_time) ((T*)a.ray_time)[ray] = total;
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of the ray times along their fixed paths with respect to the region
+// orientations: a piece of length len (cells) in region r along direction dir
+// takes len h / V(dir - theta_r), so d/dtheta_r = len h V'(dir - theta_r) / V^2,
+// with V' by an FP64 central difference of the group speed.  Each ray adds
+// dL/dT_ray times that to the gradient of its sample; consecutive pieces in one
+// region are summed before the atomic add.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void ray_grad_kernel(RayLaunch a, const T* dL_dray, double* grad)
+{
+    const long long ray = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nrays = (long long)a.nfields * a.nrec;
+    if (ray >= nrays) return;
+    const double wray = (double)dL_dray[ray];
+    const int np = a.npts[ray];
+    if (wray == 0.0 || np < 2) return;
+    const int f = (int)(ray / a.nrec);
+    const FieldDesc fd = a.fields[f];
+    const int b = fd.sample;
+    const double h = a.h_of_sample[b];
+    const double* theta = a.theta + (size_t)b * a.nregions;
+    const uint16_t* map = a.region_map + fd.map_off;
+    double* gb = grad + (size_t)b * a.nregions;
+    const T* pts = (const T*)a.pts + (size_t)ray * a.max_pts * 2;
+    int cur = -1;
+    double acc = 0.0;
+    for (int s = 0; s + 1 < np; ++s) {
+        const double x0 = pts[2 * s], y0 = pts[2 * s + 1], x1 = pts[2 * s + 2], y1 = pts[2 * s + 3];
+        const double ddx = x1 - x0, ddy = y1 - y0;
+        const double len = sqrt(ddx * ddx + ddy * ddy);
+        if (len == 0.0) continue;
+        const double dir = atan2(ddy, ddx);
+        const bool xinc = ddx > 0.0, yinc = ddy > 0.0;
+        double kx = xinc ? floor(x0 - 0.5) + 1.5 : ceil(x0 - 0.5) - 0.5;
+        double ky = yinc ? floor(y0 - 0.5) + 1.5 : ceil(y0 - 0.5) - 0.5;
+        double tprev = 0.0;
+        for (int guard = 0; guard < 1 << 20; ++guard) {
+            double tx = 2.0, ty = 2.0;
+            if (ddx != 0.0 && (xinc ? kx < x1 : kx > x1)) tx = (kx - x0) / ddx;
+            if (ddy != 0.0 && (yinc ? ky < y1 : ky > y1)) ty = (ky - y0) / ddy;
+            double tn = fmin(tx, ty);
+            const bool last = !(tn < 1.0);
+            if (last) tn = 1.0;
+            if (tn > tprev) {
+                const double tm = 0.5 * (tprev + tn);
+                int i = (int)floor(x0 + tm * ddx + 0.5), j = (int)floor(y0 + tm * ddy + 0.5);
+                i = min(max(i, 0), fd.nx - 1);
+                j = min(max(j, 0), fd.ny - 1);
+                const int r = map[(long long)j * fd.nx + i];
+                const MatD& m = a.mats[a.region_mat[r]];
+                if (!m.iso) {
+                    const double phi = dir - theta[r], e = 1e-6;
+                    const double V = group_speed64(m, a.group_model, phi);
+                    const double dV = (group_speed64(m, a.group_model, phi + e) -
+                                       group_speed64(m, a.group_model, phi - e)) / (2.0 * e);
+                    if (r != cur) {
+                        if (cur >= 0 && acc != 0.0) atomicAdd(gb + cur, wray * acc);
+                        cur = r;
+                        acc = 0.0;
+                    }
+                    acc += (tn - tprev) * len * h * dV / (V * V);
+                }
+                tprev = tn;
+            }
+            if (last) break;
+            if (tx <= ty) kx += xinc ? 1.0 : -1.0;
+            if (ty <= tx) ky += yinc ? 1.0 : -1.0;
+        }
+    }
+    if (cur >= 0 && acc != 0.0) atomicAdd(gb + cur, wray * acc);
+}
+
+cudaError_t launch_ray_gradient(int precision, const RayLaunch& a, const void* dL_dray, double* grad, int nsamples,
+                                cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)nsamples * a.nregions * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const long long nrays = (long long)a.nfields * a.nrec;
+    if (nrays == 0) return cudaSuccess;
+    const int bs = 128;
+    const long long gs = (nrays + bs - 1) / bs;
+    if (precision == ALF_FP64) ray_grad_kernel<double><<<(unsigned)gs, bs, 0, st>>>(a, (const double*)dL_dray, grad);
+    else ray_grad_kernel<float><<<(unsigned)gs, bs, 0, st>>>(a, (const float*)dL_dray, grad);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st)
 {
     const long long nrays = (long long)a.nfields * a.nrec;

@@ -107,3 +107,31 @@ def test_best_family_is_fastest_fp32_weld(api):
         out[fam] = rtime.cpu().numpy()
     best = np.minimum.reduce([out[f] for f in (1, 2, 3, 4)])
     assert np.array_equal(out[5], best)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-3)])
+def test_ray_gradient_matches_oracle(api, oracle, precision, tol):
+    """Gradient of the ray times along their fixed paths by the region orientations: the GPU's analytic
+    sum over pieces against the oracle's central differences of the path time, on the GPU's own paths."""
+    wl = W.weld_single(n=64, h=0.5e-3, rg=4, seed=9, nsrc=2, nrec=5)
+    P = api.Plan(wl, precision=precision)
+    th = P.theta_tensor()
+    times, rt = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    w = torch.linspace(0.5, 1.5, P.nsrc * P.nrec, dtype=torch.float64, device=rt.device).reshape(rt.shape)
+    g = P.ray_gradient(th, pts, npts, w).cpu().numpy()[0]
+    assert P.status() == 0
+    M = oracle_medium(oracle, wl, 0)
+    reg = wl.samples[0].region_map.reshape(-1)
+    g_o = np.zeros(wl.nregions)
+    wn = w.cpu().numpy()
+    for s in range(P.nsrc):
+        for r in range(P.nrec):
+            n = int(npts[0, s, r])
+            p = pts[0, s, r, :n].cpu().numpy().astype(np.float64)
+            g_o += wn[0, s, r] * oracle.ray_gradient(M, p, reg, wl.nregions)
+    scale = np.abs(g_o).max()
+    assert scale > 0
+    err = np.abs(g - g_o).max() / scale
+    print(f"{precision} ray gradient: max |GPU - oracle| / max|oracle| = {err:.2e}")
+    assert err < tol
