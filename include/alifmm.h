@@ -122,6 +122,10 @@ typedef struct {
                                cell-crossing times wait for the front (default 2; <= 0: no band) */
     int use_graph;          /* 1: replay the sweep rounds from a CUDA graph (default 1) */
     int time_kernels;       /* 1: time the evaluation kernel with CUDA events (alf_plan_stats; default 0) */
+    int velocity_table;     /* 1: the local update takes the qP phase speed by linear interpolation in a table
+                               of phase speeds at integer degrees (Sec. 3; Table 2 compares it with solving
+                               the Christoffel matrix at run time, 0, the default).  Group speeds (source
+                               initialisation, fallback, rays) are unchanged.  alf_backward refuses it. */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */

@@ -47,6 +47,8 @@ typedef struct {
     const om_mat* mats;
     int nmats;
     int group_model; /* 0 = the paper's group->phase inversion, 1 = exact ray velocity */
+    int vtable;      /* 1: stencil updates take the phase speed by linear interpolation in a table of phase
+                        speeds at integer degrees (Sec. 3, Sec. 4.2); 0: from the Christoffel matrix */
 } om_medium;
 
 /* counters exposed for tests */
@@ -284,7 +286,21 @@ static double stencil_time(const om_medium* M, int d, const double xa[3], const 
     double theta_n = atan2(yB - yE, xB - xE);
     double theta_p = fmod(M->theta[d] - theta_n + M_PI / 2, M_PI);
     if (theta_p < 0.0) theta_p += M_PI;
-    double v = om_phase_velocity(&M->mats[M->mat_id[d]], theta_p);
+    double v;
+    if (M->vtable) {
+        /* [R19] the table holds the qP phase speed at every integer degree of 0..180 (180-degree symmetric)
+           and is interpolated linearly in speed */
+        double deg = theta_p * 180.0 / M_PI;
+        int k = (int)floor(deg);
+        if (k < 0) k = 0;
+        if (k > 179) k = 179;
+        double f = deg - k;
+        const om_mat* m = &M->mats[M->mat_id[d]];
+        double v0 = om_phase_velocity(m, k * M_PI / 180.0), v1 = om_phase_velocity(m, (k + 1) * M_PI / 180.0);
+        v = (1.0 - f) * v0 + f * v1;
+    } else {
+        v = om_phase_velocity(&M->mats[M->mat_id[d]], theta_p);
+    }
     return tB + FD * M->h / v;
 }
 

@@ -44,7 +44,7 @@ class Mat(C.Structure):
 class Medium(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double),
                 ("mat_id", C.POINTER(C.c_int32)), ("theta", C.POINTER(C.c_double)),
-                ("mats", C.POINTER(Mat)), ("nmats", C.c_int), ("group_model", C.c_int)]
+                ("mats", C.POINTER(Mat)), ("nmats", C.c_int), ("group_model", C.c_int), ("vtable", C.c_int)]
 
 
 class RayOpts(C.Structure):
@@ -149,21 +149,23 @@ def diamond_table() -> np.ndarray:
 class OMedium:
     """A medium on an nx x ny grid: per-node material index and orientation."""
 
-    def __init__(self, nx, ny, h, mat_id, theta, mats, group_model=GROUP_PAPER):
+    def __init__(self, nx, ny, h, mat_id, theta, mats, group_model=GROUP_PAPER, vtable=0):
         self.nx, self.ny, self.h = int(nx), int(ny), float(h)
         self.mat_id = np.ascontiguousarray(mat_id, dtype=np.int32).reshape(ny * nx)
         self.theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(ny * nx)
         self._mats = (Mat * len(mats))(*mats)
         self.mats = list(mats)
         self.group_model = int(group_model)
+        self.vtable = int(vtable)
         self.c = Medium(self.nx, self.ny, self.h, _ptr(self.mat_id, C.c_int32), _ptr(self.theta, C.c_double),
-                        self._mats, len(mats), self.group_model)
+                        self._mats, len(mats), self.group_model, self.vtable)
 
     @classmethod
-    def from_regions(cls, nx, ny, h, region_map, region_theta, region_material, mats, group_model=GROUP_PAPER):
+    def from_regions(cls, nx, ny, h, region_map, region_theta, region_material, mats, group_model=GROUP_PAPER,
+                     vtable=0):
         rm = np.asarray(region_map).reshape(ny, nx).astype(np.int64)
         return cls(nx, ny, h, np.asarray(region_material)[rm], np.asarray(region_theta, np.float64)[rm], mats,
-                   group_model)
+                   group_model, vtable)
 
 
 def init_radius(M: OMedium, si: int, sj: int, r0: int):
@@ -261,8 +263,8 @@ def ray_gradient(M: OMedium, pts, region_of_node, nregions, eps=1e-6):
         tp, tm = M.theta.copy(), M.theta.copy()
         tp[reg == r] += eps
         tm[reg == r] -= eps
-        Mp = OMedium(M.nx, M.ny, M.h, M.mat_id, tp, M.mats, M.group_model)
-        Mm = OMedium(M.nx, M.ny, M.h, M.mat_id, tm, M.mats, M.group_model)
+        Mp = OMedium(M.nx, M.ny, M.h, M.mat_id, tp, M.mats, M.group_model, M.vtable)
+        Mm = OMedium(M.nx, M.ny, M.h, M.mat_id, tm, M.mats, M.group_model, M.vtable)
         g[r] = (path_time(Mp, pts) - path_time(Mm, pts)) / (2 * eps)
     return g
 

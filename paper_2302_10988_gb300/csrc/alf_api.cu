@@ -262,6 +262,8 @@ static void plan_free(alf_plan* p)
     dfree(p->d_rec);
     dfree(p->d_regions);
     dfree(p->d_regions_rays);
+    dfree(p->d_vtab);
+    dfree(p->d_vtab64);
     dfree(p->d_regions64);
     dfree(p->d_q);
     dfree(p->d_ray_error);
@@ -301,6 +303,8 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     }
     if (opt.sweep < 0 || opt.sweep > 3) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1, 2 or 3");
     if (opt.ray_family < 0 || opt.ray_family > 5) return fail(ctx, ALF_ERR_INVALID_ARG, "ray_family must be in 0..5");
+    if (opt.velocity_table != 0 && opt.velocity_table != 1)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table must be 0 or 1");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
@@ -511,6 +515,12 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         char* r3 = nullptr;
         ALLOC(r3, (size_t)p->B * p->R * rsz);
         p->d_regions_rays = r3;
+        if (opt.velocity_table) {
+            char* t1 = nullptr;
+            ALLOC(t1, (size_t)p->nmat * ALF_VTAB_N * (opt.precision == ALF_FP64 ? 8 : 4));
+            p->d_vtab = t1;
+            ALLOC(p->d_vtab64, (size_t)p->nmat * ALF_VTAB_N);
+        }
     }
 #undef ALLOC
     if (cudaMallocHost((void**)&p->h_q, sizeof(QueueState)) != cudaSuccess ||
@@ -537,6 +547,32 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (e == cudaSuccess) e = up(p->d_bm_off, bm_off.data(), bm_off.size() * sizeof(size_t));
     if (e == cudaSuccess) e = up(p->d_region_mat, g->region_material, (size_t)p->R * sizeof(uint16_t));
     if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
+    if (e == cudaSuccess && opt.velocity_table) {
+        // phase speed of every material at 0..180 degrees from its axis (the qP eigenvalue of the rotated
+        // Christoffel matrix, Sec. 3.2)
+        std::vector<double> t64((size_t)p->nmat * ALF_VTAB_N);
+        for (int m = 0; m < p->nmat; ++m)
+            for (int k = 0; k < ALF_VTAB_N; ++k) {
+                const MatD& q = mats[m];
+                double lam = q.a22;
+                if (!q.iso) {
+                    const double th = k * 3.141592653589793 / 180.0, c = std::cos(th), sn = std::sin(th);
+                    const double al = c * c * q.a22 + sn * sn * q.a44, ga = c * c * q.a44 + sn * sn * q.a33;
+                    const double be = c * sn * (q.a23 + q.a44);
+                    lam = 0.5 * ((al + ga) + std::sqrt((al - ga) * (al - ga) + 4.0 * be * be));
+                }
+                t64[(size_t)m * ALF_VTAB_N + k] = std::sqrt(lam);
+            }
+        e = up(p->d_vtab64, t64.data(), t64.size() * sizeof(double));
+        if (e == cudaSuccess) {
+            if (opt.precision == ALF_FP64) {
+                e = up(p->d_vtab, t64.data(), t64.size() * sizeof(double));
+            } else {
+                std::vector<float> t32(t64.begin(), t64.end());
+                e = up(p->d_vtab, t32.data(), t32.size() * sizeof(float));
+            }
+        }
+    }
     if (e == cudaSuccess) e = up(p->d_h, g->h, (size_t)p->B * sizeof(double));
     if (e == cudaSuccess && p->Rr) e = up(p->d_rec, g->rec_ij, (size_t)p->B * p->Rr * 2 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(p->d_ray_error, 0, 4 * sizeof(unsigned));
@@ -586,7 +622,8 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     cudaStream_t st = as_stream(stream);
     const int prec = p->opt.precision;
     const int gm = p->opt.group_model;
-    ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm, p->d_regions, st));
+    ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm, p->d_regions, st,
+                                      p->d_vtab));
     ALF_CUDA(ctx, launch_fill_inf(prec, times, p->total_nodes, st));
     if (records) ALF_CUDA(ctx, cudaMemsetAsync(records, 255, p->total_nodes, st));
     ALF_CUDA(ctx, cudaMemsetAsync(p->d_frozen, 0, sizeof(unsigned) * (size_t)p->nfields * frozen_words(p->box), st));
@@ -688,7 +725,7 @@ alf_status alf_check64(alf_plan* p, const double* theta, const void* times, cons
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);
     ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
-                                      p->opt.group_model, p->d_regions64, st));
+                                      p->opt.group_model, p->d_regions64, st, p->d_vtab64));
     ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
                                  records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st));
     return ALF_OK;
@@ -776,6 +813,8 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: the plan was created without keep_records");
     if (p->opt.init_mode != ALF_INIT_RADIUS)
         return fail(ctx, ALF_ERR_UNSUPPORTED, "alf_backward: only the straight-ray initialisation is differentiated");
+    if (p->opt.velocity_table)
+        return fail(ctx, ALF_ERR_UNSUPPORTED, "alf_backward: the velocity-table update is not differentiated");
     if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_backward: plan has no receivers");
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);

@@ -34,6 +34,7 @@ struct RegionP {
     T h;
     int iso;
     int pad;
+    const T* vtab;  // velocity-table mode: qP phase speed of the region's material at 0..180 degrees, else null
 };
 
 struct MatD {   // per material, FP64, c / rho
@@ -107,12 +108,27 @@ ALF_D double sqrt_(double v) { return sqrt(v); }
 // tau_D = tau_B + h |(D - E) x u| / sqrt(|u|^2 lambda/rho).
 // ---------------------------------------------------------------------------
 // |u|^2 * (qP lambda / rho) for the wavefront direction u (normal (-u_y, u_x)).
+ALF_D float atan2_(float y, float x) { return atan2f(y, x); }
+ALF_D double atan2_(double y, double x) { return atan2(y, x); }
+
 template <typename T>
 ALF_D T phase_L(const RegionP<T>& R, T ux, T uy)
 {
     if (R.iso) return R.a22 * (ux * ux + uy * uy);
     const T C = R.sth * ux - R.cth * uy;
     const T S = R.cth * ux + R.sth * uy;
+    if (R.vtab) {
+        // velocity-table mode (Sec. 3, Sec. 4.2): the phase speed at the normal's angle from the material
+        // axis, linearly interpolated between the table's integer degrees (180-degree symmetric)
+        T deg = atan2_(S, C) * T(57.295779513082320876);
+        if (deg < T(0)) deg += T(180);
+        if (deg >= T(180)) deg -= T(180);
+        int k = (int)floor(deg);
+        k = k < 0 ? 0 : (k > 179 ? 179 : k);
+        const T f = deg - T(k);
+        const T v = (T(1) - f) * R.vtab[k] + f * R.vtab[k + 1];
+        return (ux * ux + uy * uy) * v * v;
+    }
     const T CC = C * C, SS = S * S;
     const T al = CC * R.a22 + SS * R.a44;
     const T ga = CC * R.a44 + SS * R.a33;

@@ -60,9 +60,11 @@ struct FimLaunch {
 };
 
 // kernels (alf_kernels.cu)
+// velocity table: the qP phase speed at 0, 1, ..., 180 degrees from the material axis, per material
+#define ALF_VTAB_N 181
 cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t* region_mat, const double* theta,
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
-                                cudaStream_t st);
+                                cudaStream_t st, const void* vtab = nullptr);
 cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st);
 cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fields, int nfields,
                                const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
@@ -219,6 +221,8 @@ struct alf_plan {
     int32_t* d_rec = nullptr;
     void* d_regions = nullptr;    // RegionP<T> of the plan precision
     void* d_regions64 = nullptr;  // RegionP<double> for the FP64 check
+    void* d_vtab = nullptr;          // velocity tables of the plan precision (option velocity_table)
+    double* d_vtab64 = nullptr;      // the same in FP64, for the FP64 check
     void* d_regions_rays = nullptr;  // RegionP<T> of the ray tracer (its own copy: rays may overlap the others)
     // sweep workspace
     unsigned* d_list0 = nullptr;

@@ -47,7 +47,7 @@ ALF_D T load_cg(const T* p)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void prep_regions_kernel(const MatD* mats, const uint16_t* region_mat, const double* theta, const double* h,
-                                    int nsamples, int nregions, int group_model, RegionP<T>* out)
+                                    int nsamples, int nregions, int group_model, RegionP<T>* out, const T* vtab)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nsamples * nregions) return;
@@ -76,21 +76,22 @@ __global__ void prep_regions_kernel(const MatD* mats, const uint16_t* region_mat
     R.h = T(hb);
     R.iso = m.iso;
     R.pad = 0;
+    R.vtab = vtab ? vtab + (size_t)region_mat[r] * ALF_VTAB_N : nullptr;
     out[k] = R;
 }
 
 cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t* region_mat, const double* theta,
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
-                                cudaStream_t st)
+                                cudaStream_t st, const void* vtab)
 {
     const int n = nsamples * nregions;
     const int bs = 128, gs = (n + bs - 1) / bs;
     if (precision == ALF_FP64)
         prep_regions_kernel<double><<<gs, bs, 0, st>>>(mats, region_mat, theta, h, nsamples, nregions, group_model,
-                                                       (RegionP<double>*)regions_out);
+                                                       (RegionP<double>*)regions_out, (const double*)vtab);
     else
         prep_regions_kernel<float><<<gs, bs, 0, st>>>(mats, region_mat, theta, h, nsamples, nregions, group_model,
-                                                      (RegionP<float>*)regions_out);
+                                                      (RegionP<float>*)regions_out, (const float*)vtab);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -1,0 +1,91 @@
+"""Velocity-table mode (option velocity_table): the local update takes the qP phase speed by linear
+interpolation in a table of phase speeds at integer degrees (Sec. 3 and Sec. 4.2; Table 2 compares it with
+solving the Christoffel matrix at run time)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2302_10988_gb300 import workloads as W
+from tests.gpu_helpers import record_mismatch, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2302_10988_gb300 import build
+    build.build()
+    from paper_2302_10988_gb300 import api as A
+    return A
+
+
+def _oracle(oracle, wl, s):
+    smp = wl.samples[0]
+    mats = [oracle.mat_from_voigt(c6, rho) for c6, rho in wl.materials]
+    M = oracle.OMedium.from_regions(smp.nx, smp.ny, smp.h, smp.region_map, smp.region_theta, wl.region_material,
+                                    mats, vtable=1)
+    fr, t0 = oracle.init_radius(M, *(int(v) for v in smp.src[s]), 2)
+    tau, rec, st = oracle.fmm(M, fr, t0)
+    return tau, rec, fr.reshape(tau.shape)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
+def test_velocity_table_matches_oracle(api, oracle, precision, tol):
+    wl = W.weld_single(n=80, h=0.5e-3, rg=5, seed=13, nsrc=3, nrec=4)
+    P = api.Plan(wl, precision=precision, velocity_table=1)
+    th = P.theta_tensor()
+    rec = P.new_records()
+    times, rt = P.solve(th, records=rec)
+    assert P.status() == 0
+    flips = 0
+    for s in range(3):
+        tau, orec, fr = _oracle(oracle, wl, s)
+        e = rel_err(P.field(times, s).cpu().numpy(), tau)
+        assert e.max() < tol, (s, e.max())
+        flips += record_mismatch(P.field(rec, s).cpu().numpy(), orec, fr)
+    if precision == "fp64":
+        assert flips == 0
+    mr, fl = P.check64(th, times, rec)
+    torch.cuda.synchronize()
+    assert mr.max().item() < (1e-12 if precision == "fp64" else 1e-4)
+
+
+def test_table2_velocity_table_row_on_gpu(api, oracle):
+    """Sec. 4.5, Table 2 (ALI-FMM with the velocity table): mean absolute relative error on the 21 x 21 cubic
+    steel grid for sub-grid sizes 1 and 3, within +-10 % of the printed values."""
+    ref = {1: 1.083, 3: 1.073}  # Table 2, row "ALI-FMM" (velocity table)
+    c6, rho = W.PAPER_CUBIC
+    m = oracle.mat_from_voigt(c6, rho)
+    for s in (1, 3):
+        n = 20 * s + 1
+        dens, rad = ((27, 9, 3), (1, 6, 13)) if s == 1 else ((9, 3), (2 * s, 5 * s))
+        smp = W.Sample(n, n, 1e-3 / s, np.zeros((n, n), np.uint16), np.array([0.0]),
+                       np.array([[10 * s, 10 * s]], np.int32), np.array([[n - 1, n - 1]], np.int32))
+        wl = W.Workload("table 2", [W.PAPER_CUBIC], np.array([0], np.uint16), [smp])
+        P = api.Plan(wl, precision="fp64", init_mode=1, n_levels=len(dens), level_density=dens, level_radius=rad,
+                     velocity_table=1)
+        times, _ = P.solve(P.theta_tensor())
+        assert P.status() == 0
+        sub = P.field(times, 0).cpu().numpy()[::s, ::s]
+        jj, ii = np.mgrid[0:21, 0:21]
+        d = np.hypot(ii - 10, jj - 10) * 1e-3
+        V = np.array([oracle.group_exact(m, a)[1] for a in np.arctan2(jj - 10, ii - 10).ravel()]).reshape(21, 21)
+        T = d / np.where(d > 0, V, 1.0)
+        e = 100.0 * (np.abs(sub - T)[d > 0] / T[d > 0]).mean()
+        print(f"Table 2 velocity table, sub-grid {s}: GPU {e:.3f} %, paper {ref[s]:.3f} %")
+        assert abs(e / ref[s] - 1.0) < 0.10
+
+
+def test_velocity_table_backward_is_refused(api):
+    from paper_2302_10988_gb300 import binding as B
+    wl = W.weld_single(n=40, h=0.5e-3, rg=4, seed=5, nsrc=2, nrec=2)
+    P = api.Plan(wl, precision="fp32", velocity_table=1, keep_records=1)
+    th = P.theta_tensor()
+    rec = P.new_records()
+    times, rt = P.solve(th, records=rec)
+    with pytest.raises(B.AlfError) as e:
+        P.backward(th, times, rec, rt)
+    assert e.value.code == 8

@@ -172,3 +172,53 @@ def test_reciprocity(oracle):
             if a < b:
                 ta, tb = fields[a][b[1], b[0]], fields[b][a[1], a[0]]
                 assert abs(ta - tb) / ta < 0.02
+
+
+def test_table2_velocity_table_band(oracle):
+    """Sec. 4.5, Table 2, row "ALI-FMM" (phase speeds from a table at integer degrees, linearly
+    interpolated): mean abs relative error for sub-grid sizes 1, 3, 5, 7 within +-10 % of the printed
+    values.  (The paper finds the table slightly less accurate than the run-time solve; here the two differ
+    by less than 1 %, in either direction.)"""
+    ref = {1: 1.083, 3: 1.073, 5: 0.715, 7: 0.565}  # Table 2, velocity-table row
+    c6, rho = W.PAPER_CUBIC
+    m = oracle.mat_from_voigt(c6, rho)
+    for s in (1, 3, 5, 7):
+        n = 20 * s + 1
+        M = oracle.OMedium(n, n, 1e-3 / s, np.zeros(n * n), np.zeros(n * n), [m], vtable=1)
+        dens, rad = ((27, 9, 3), (1, 6, 13)) if s == 1 else ((9, 3), (2 * s, 5 * s))
+        fr, t0 = oracle.init_hierarchy(M, 10 * s, 10 * s, dens, rad)
+        tau = oracle.fmm(M, fr, t0)[0]
+        sub = tau[::s, ::s]
+        jj, ii = np.mgrid[0:21, 0:21]
+        d = np.hypot(ii - 10, jj - 10) * 1e-3
+        V = np.array([oracle.group_exact(m, a)[1] for a in np.arctan2(jj - 10, ii - 10).ravel()]).reshape(21, 21)
+        T = d / np.where(d > 0, V, 1.0)
+        e = 100.0 * (np.abs(sub - T)[d > 0] / T[d > 0]).mean()
+        assert abs(e / ref[s] - 1.0) < 0.10, (s, e, ref[s])
+
+
+def test_velocity_table_exact_at_integer_degrees(oracle):
+    """At integer degrees the table holds the Christoffel speed itself: a plane wave whose normal is at
+    0, 45 or 90 degrees from the axis of a homogeneous medium gets the same update with and without it."""
+    c6, rho = W.WELD_TI
+    m = oracle.mat_from_voigt(c6, rho)
+    n = 9
+    for th_deg in (0.0, 45.0, 90.0):
+        th = np.radians(th_deg)
+        M0 = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m])
+        M1 = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m], vtable=1)
+        jj, ii = np.mgrid[0:n, 0:n]
+        tau = (ii * 1e-3 / 5000.0).astype(np.float64)  # plane wave along +x: normal at -th from the axis
+        for row in (1, 3, 4, 6):  # rows whose A, B, C are not all on one wavefront of this plane wave
+            a = oracle.stencil_value(M0, tau.reshape(-1), 4, 4, row)
+            b = oracle.stencil_value(M1, tau.reshape(-1), 4, 4, row)
+            assert a == pytest.approx(b, rel=1e-12), (th_deg, row)
+    # between integer degrees the table interpolates: close to, but not equal to, the run-time solve
+    th = np.radians(30.5)
+    M0 = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m])
+    M1 = oracle.OMedium(n, n, 1e-3, np.zeros(n * n), np.full(n * n, th), [m], vtable=1)
+    jj, ii = np.mgrid[0:n, 0:n]
+    tau = (ii * 1e-3 / 5000.0).astype(np.float64)
+    a = oracle.stencil_value(M0, tau.reshape(-1), 4, 4, 1)
+    b = oracle.stencil_value(M1, tau.reshape(-1), 4, 4, 1)
+    assert a != b and abs(b / a - 1) < 1e-4
