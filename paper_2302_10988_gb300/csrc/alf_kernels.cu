@@ -972,6 +972,7 @@ __global__ void eval_velocity_kernel(const MatD* mat, int kind, int group_model,
             R.cth = 1.0f;
             R.sth = 0.0f;
             R.iso = m.iso;
+            R.vtab = nullptr;  // the run-time Christoffel solve
             // a unit wavefront direction u whose normal (-u_y, u_x) is at angle a
             out[k] = (double)sqrtf(phase_L<float>(R, float(s), -float(c)));
         }
