@@ -409,7 +409,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     p->warp_words = (unsigned)((p->max_field_nodes + 31) / 32);
     p->warp_grid = 0;
     if (p->max_field_nodes <= (size_t(1) << 18)) {
-        const int c = fim_warp_ctas_per_sm(opt.precision, p->warp_words);
+        const int c = fim_warp_ctas_per_sm(opt.precision, p->warp_words, opt.velocity_table != 0);
         p->warp_grid = c > 0 ? c * ctx->nsm : 0;
     }
     if (opt.sweep == 2 && p->warp_grid == 0) {
@@ -421,7 +421,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
     if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
     {
-        const int c = fim_cta_ctas_per_sm(opt.precision, p->cta_words);
+        const int c = fim_cta_ctas_per_sm(opt.precision, p->cta_words, opt.velocity_table != 0);
         p->cta_grid = std::max(1, c) * ctx->nsm;
     }
     p->sweep_mode = opt.sweep != 0 ? opt.sweep
@@ -657,6 +657,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
         h.q = p->d_q;
         h.band_cells = p->opt.band_cells;
         h.max_rounds_per_node = (unsigned)p->opt.max_rounds;
+        h.vtable = p->opt.velocity_table;
         ALF_CUDA(ctx, launch_init_hierarchy(prec, h, st));
     } else {
         ALF_CUDA(ctx, launch_init_radius(prec, times, p->d_fields, p->nfields, p->d_map, p->d_region_mat, p->d_mats,
@@ -687,6 +688,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     a.band_cells = p->opt.band_cells;
     a.q = p->d_q;
     a.records = records;
+    a.vtable = p->opt.velocity_table;
     if (p->sweep_mode == 2 || p->sweep_mode == 3) {
         // field-resident sweep: the whole fixed-point iteration in one launch
         const bool timing = p->opt.time_kernels != 0;

@@ -111,13 +111,13 @@ ALF_D double sqrt_(double v) { return sqrt(v); }
 ALF_D float atan2_(float y, float x) { return atan2f(y, x); }
 ALF_D double atan2_(double y, double x) { return atan2(y, x); }
 
-template <typename T>
+template <typename T, bool VT = false>
 ALF_D T phase_L(const RegionP<T>& R, T ux, T uy)
 {
     if (R.iso) return R.a22 * (ux * ux + uy * uy);
     const T C = R.sth * ux - R.cth * uy;
     const T S = R.cth * ux + R.sth * uy;
-    if (R.vtab) {
+    if constexpr (VT) {
         // velocity-table mode (Sec. 3, Sec. 4.2): the phase speed at the normal's angle from the material
         // axis, linearly interpolated between the table's integer degrees (180-degree symmetric)
         T deg = atan2_(S, C) * T(57.295779513082320876);
@@ -142,7 +142,7 @@ ALF_D double div_(double a, double b) { return a / b; }
 ALF_D float rsqrt_(float v) { return rsqrtf(v); }
 ALF_D double rsqrt_(double v) { return 1.0 / sqrt(v); }
 
-template <typename T>
+template <typename T, bool VT = false>
 ALF_D T stencil_time(int xA, int yA, int xB, int yB, int xC, int yC, T tA, T tB, T tC, const RegionP<T>& R)
 {
     const T a = div_(tB - tA, tC - tA);
@@ -150,7 +150,7 @@ ALF_D T stencil_time(int xA, int yA, int xB, int yB, int xC, int yC, T tA, T tB,
     const T Ey = T(yA) + a * T(yC - yA);
     const T ux = T(xB) - Ex, uy = T(yB) - Ey;
     const T cross = abs_(T(yB) * Ex - T(xB) * Ey);
-    return tB + R.h * cross * rsqrt_(phase_L(R, ux, uy));
+    return tB + R.h * cross * rsqrt_(phase_L<T, VT>(R, ux, uy));
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +240,8 @@ ALF_HD int pair_q(int p)
 // that satisfies it is c(u) - 1.  So the walk visits only the steps where U
 // can change and stops as soon as c(u) - 1 comes before the next of them.
 // ---------------------------------------------------------------------------
-template <typename T>
+// VT: the velocity-table mode (the table lookup is compiled only into the kernels that use it)
+template <typename T, bool VT = false>
 ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
 {
     (void)me;
@@ -298,7 +299,7 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
             const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
             const int xB = m1 ? sdi(P) : sdi(Q), yB = m1 ? sdj(P) : sdj(Q);
             const int xC = m1 ? sdi(Q) : sdi(P), yC = m1 ? sdj(Q) : sdj(P);
-            const T v = stencil_time<T>(sdi(A), sdj(A), xB, yB, xC, yC, tA, tB, tC, R);
+            const T v = stencil_time<T, VT>(sdi(A), sdj(A), xB, yB, xC, yC, tA, tB, tC, R);
             if (v > tC) {
                 pv[p] = v;
                 pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));

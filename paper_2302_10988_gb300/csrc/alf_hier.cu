@@ -79,7 +79,7 @@ size_t hier_scratch_bytes(int precision, size_t L)
     return (bytes + 255) / 256 * 256;
 }
 
-template <typename T>
+template <typename T, bool VT>
 __global__ void __launch_bounds__(128) hier_kernel(HierLaunch a)
 {
     extern __shared__ unsigned s_hbm[];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(128) hier_kernel(HierLaunch a)
             const unsigned nact = warp_seed_square(g, -a0, -b0, reach);
             unsigned long long evals = 0ull;
             unsigned rounds = 0u;
-            if (!warp_sweep(g, nact, evals, rounds)) {
+            if (!warp_sweep<T, VT>(g, nact, evals, rounds)) {
                 if (lane == 0) atomicCAS(&a.q->error, 0u, (unsigned)ALF_ERR_NOT_CONVERGED);
                 return;
             }
@@ -234,25 +234,26 @@ __global__ void __launch_bounds__(128) hier_kernel(HierLaunch a)
     }
 }
 
-template <typename T>
+template <typename T, bool VT>
 static cudaError_t hier_t(const HierLaunch& a, cudaStream_t st)
 {
     const int wpb = 4;
     const size_t smem = (size_t)wpb * ((a.level_cap + 31) / 32) * sizeof(unsigned);
     if (smem > 48 * 1024) {
         const cudaError_t e =
-            cudaFuncSetAttribute(hier_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(hier_kernel<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int grid = (a.nwarps + wpb - 1) / wpb;
-    hier_kernel<T><<<grid, wpb * 32, smem, st>>>(a);
+    hier_kernel<T, VT><<<grid, wpb * 32, smem, st>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_hierarchy(int precision, const HierLaunch& a, cudaStream_t st)
 {
-    return precision == ALF_FP64 ? hier_t<double>(a, st) : hier_t<float>(a, st);
+    if (a.vtable) return precision == ALF_FP64 ? hier_t<double, true>(a, st) : hier_t<float, true>(a, st);
+    return precision == ALF_FP64 ? hier_t<double, false>(a, st) : hier_t<float, false>(a, st);
 }
 
 }  // namespace alf

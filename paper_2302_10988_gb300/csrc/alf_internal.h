@@ -57,6 +57,7 @@ struct FimLaunch {
     double band_cells;             // evaluation band beyond the front, in cells of cell_time (<= 0: none)
     QueueState* q;
     uint8_t* records;
+    int vtable;                    // the regions carry velocity tables (kernels compiled with the lookup)
 };
 
 // kernels (alf_kernels.cu)
@@ -82,11 +83,11 @@ cudaError_t launch_fim_pending(const FimLaunch& a, int parity, unsigned long lon
 #define ALF_SWEEP_WARPS 4
 cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* order, unsigned words_per_warp,
                             int grid, cudaStream_t st);
-int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp);  // 0: does not fit
+int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp, bool vt);  // 0: does not fit
 // field-resident sweep by a CTA per field (few large fields); bitmaps of up to smem_words words in shared memory
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                            cudaStream_t st);
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words);
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -123,6 +124,7 @@ struct HierLaunch {
     QueueState* q;           // error word
     double band_cells;
     unsigned max_rounds_per_node;
+    int vtable;
 };
 size_t hier_scratch_bytes(int precision, size_t level_cap);
 cudaError_t launch_init_hierarchy(int precision, const HierLaunch& a, cudaStream_t st);

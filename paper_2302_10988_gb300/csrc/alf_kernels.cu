@@ -344,7 +344,7 @@ ALF_D int field_of(const unsigned* eoff, int nfields, unsigned e)
     return lo;
 }
 
-template <typename T, int NT>
+template <typename T, int NT, bool VT>
 __global__ void __launch_bounds__(NT) fim_eval_kernel(FimLaunch a)
 {
     const unsigned E = a.eoff[a.nfields];
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(NT) fim_eval_kernel(FimLaunch a)
         const T old = __ldcg(tf + n);
         const RegionP<T> R = regions[(size_t)fd.sample * a.nregions + __ldg(a.region_map + fd.map_off + n)];
         int rec;
-        const T v = local_F<T>(nb, (int)n, nx, R, rec);
+        const T v = local_F<T, VT>(nb, (int)n, nx, R, rec);
         if (a.records) a.records[fd.node_off + n] = (uint8_t)rec;
         if (!same_bits(v, old)) __stcg(tf + n, v);
         oldv[e] = old;
@@ -449,7 +449,7 @@ __global__ void fim_pending_kernel(FimLaunch a, int parity, unsigned long long* 
 // h / d, `scale` = 1 / d).
 // ---------------------------------------------------------------------------
 // FP32: registers capped so that four 4-warp CTAs fit an SM (what the shared bitmaps of 320 x 320 fields allow)
-template <typename T, int NW>
+template <typename T, int NW, bool VT>
 __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
     fim_warp_kernel(FimLaunch a, const unsigned* order, unsigned words_per_warp)
 {
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
         const unsigned nact = warp_seed_square(g, fd.si, fd.sj, a.box + 2);
         unsigned long long evals = 0ull;
         unsigned rounds = 0u;
-        const bool ok = warp_sweep(g, nact, evals, rounds);
+        const bool ok = warp_sweep<T, VT>(g, nact, evals, rounds);
         if (lane == 0) {
             if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
 
 // Field-resident sweep by a whole CTA (few large fields): the same rounds, block barriers between the
 // steps.  The dirty bitmap is in shared memory when the field's fits, else in the field's global bitmap.
-template <typename T, int NT>
+template <typename T, int NT, bool VT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fim_cta_kernel(FimLaunch a, const unsigned* order, unsigned smem_words)
 {
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         const unsigned nact = cta_seed_square<T, NT>(g, fd.si, fd.sj, a.box + 2, sh);
         unsigned long long evals = 0ull;
         unsigned rounds = 0u;
-        const bool ok = cta_sweep<T, NT>(g, nact, evals, rounds, sh);
+        const bool ok = cta_sweep<T, NT, VT>(g, nact, evals, rounds, sh);
         if (threadIdx.x == 0) {
             if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
@@ -553,23 +553,23 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 
 #define ALF_CTA_THREADS 256
 
-template <typename T>
+template <typename T, bool VT>
 static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
 {
     *smem = (size_t)smem_words * sizeof(unsigned);
     if (*smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fim_cta_kernel<T, ALF_CTA_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fim_cta_kernel<T, ALF_CTA_THREADS, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)*smem);
 }
 
-template <typename T>
+template <typename T, bool VT>
 static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                              cudaStream_t st)
 {
     size_t smem = 0;
-    cudaError_t e = fim_cta_smem<T>(smem_words, &smem);
+    cudaError_t e = fim_cta_smem<T, VT>(smem_words, &smem);
     if (e != cudaSuccess) return e;
-    fim_cta_kernel<T, ALF_CTA_THREADS><<<grid, ALF_CTA_THREADS, smem, st>>>(a, order, smem_words);
+    fim_cta_kernel<T, ALF_CTA_THREADS, VT><<<grid, ALF_CTA_THREADS, smem, st>>>(a, order, smem_words);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -577,45 +577,49 @@ static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                            cudaStream_t st)
 {
-    return precision == ALF_FP64 ? fim_cta_t<double>(a, order, smem_words, grid, st)
-                                 : fim_cta_t<float>(a, order, smem_words, grid, st);
+    if (a.vtable)
+        return precision == ALF_FP64 ? fim_cta_t<double, true>(a, order, smem_words, grid, st)
+                                     : fim_cta_t<float, true>(a, order, smem_words, grid, st);
+    return precision == ALF_FP64 ? fim_cta_t<double, false>(a, order, smem_words, grid, st)
+                                 : fim_cta_t<float, false>(a, order, smem_words, grid, st);
 }
 
-template <typename T>
+template <typename T, bool VT>
 static int fim_cta_occ(unsigned smem_words)
 {
     size_t smem = 0;
-    if (fim_cta_smem<T>(smem_words, &smem) != cudaSuccess) return 0;
+    if (fim_cta_smem<T, VT>(smem_words, &smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, ALF_CTA_THREADS>, ALF_CTA_THREADS,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, ALF_CTA_THREADS, VT>, ALF_CTA_THREADS,
                                                       smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words)
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt)
 {
-    return precision == ALF_FP64 ? fim_cta_occ<double>(smem_words) : fim_cta_occ<float>(smem_words);
+    if (vt) return precision == ALF_FP64 ? fim_cta_occ<double, true>(smem_words) : fim_cta_occ<float, true>(smem_words);
+    return precision == ALF_FP64 ? fim_cta_occ<double, false>(smem_words) : fim_cta_occ<float, false>(smem_words);
 }
 
 // dynamic shared memory of the field-resident sweep: one dirty bitmap per warp
-template <typename T>
+template <typename T, bool VT>
 static cudaError_t fim_warp_smem(unsigned words_per_warp, size_t* smem)
 {
     *smem = (size_t)ALF_SWEEP_WARPS * words_per_warp * sizeof(unsigned);
     if (*smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fim_warp_kernel<T, ALF_SWEEP_WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fim_warp_kernel<T, ALF_SWEEP_WARPS, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)*smem);
 }
 
-template <typename T>
+template <typename T, bool VT>
 static cudaError_t fim_warp_t(const FimLaunch& a, const unsigned* order, unsigned words_per_warp, int grid,
                               cudaStream_t st)
 {
     size_t smem = 0;
-    cudaError_t e = fim_warp_smem<T>(words_per_warp, &smem);
+    cudaError_t e = fim_warp_smem<T, VT>(words_per_warp, &smem);
     if (e != cudaSuccess) return e;
-    fim_warp_kernel<T, ALF_SWEEP_WARPS><<<grid, ALF_SWEEP_WARPS * 32, smem, st>>>(a, order, words_per_warp);
+    fim_warp_kernel<T, ALF_SWEEP_WARPS, VT><<<grid, ALF_SWEEP_WARPS * 32, smem, st>>>(a, order, words_per_warp);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -623,25 +627,30 @@ static cudaError_t fim_warp_t(const FimLaunch& a, const unsigned* order, unsigne
 cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* order, unsigned words_per_warp,
                             int grid, cudaStream_t st)
 {
-    return precision == ALF_FP64 ? fim_warp_t<double>(a, order, words_per_warp, grid, st)
-                                 : fim_warp_t<float>(a, order, words_per_warp, grid, st);
+    if (a.vtable)
+        return precision == ALF_FP64 ? fim_warp_t<double, true>(a, order, words_per_warp, grid, st)
+                                     : fim_warp_t<float, true>(a, order, words_per_warp, grid, st);
+    return precision == ALF_FP64 ? fim_warp_t<double, false>(a, order, words_per_warp, grid, st)
+                                 : fim_warp_t<float, false>(a, order, words_per_warp, grid, st);
 }
 
-template <typename T>
+template <typename T, bool VT>
 static int fim_warp_occ(unsigned words_per_warp)
 {
     size_t smem = 0;
-    if (fim_warp_smem<T>(words_per_warp, &smem) != cudaSuccess) return 0;
+    if (fim_warp_smem<T, VT>(words_per_warp, &smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_warp_kernel<T, ALF_SWEEP_WARPS>, ALF_SWEEP_WARPS * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_warp_kernel<T, ALF_SWEEP_WARPS, VT>, ALF_SWEEP_WARPS * 32,
                                                       smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp)
+int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp, bool vt)
 {
-    return precision == ALF_FP64 ? fim_warp_occ<double>(words_per_warp) : fim_warp_occ<float>(words_per_warp);
+    if (vt)
+        return precision == ALF_FP64 ? fim_warp_occ<double, true>(words_per_warp) : fim_warp_occ<float, true>(words_per_warp);
+    return precision == ALF_FP64 ? fim_warp_occ<double, false>(words_per_warp) : fim_warp_occ<float, false>(words_per_warp);
 }
 
 template <typename T>
@@ -651,8 +660,13 @@ static cudaError_t fim_round_t(const FimLaunch& a, int parity, int grid_fields, 
     fim_prep_kernel<T><<<grid_fields, 256, 0, st>>>(a, parity);
     fim_scan_kernel<<<1, 1024, 0, st>>>(a);
     if (ev0) cudaEventRecord(ev0, st);
-    if (eval_block == 256) fim_eval_kernel<T, 256><<<grid_eval / 2, 256, 0, st>>>(a);
-    else fim_eval_kernel<T, 128><<<grid_eval, 128, 0, st>>>(a);
+    if (a.vtable) {
+        if (eval_block == 256) fim_eval_kernel<T, 256, true><<<grid_eval / 2, 256, 0, st>>>(a);
+        else fim_eval_kernel<T, 128, true><<<grid_eval, 128, 0, st>>>(a);
+    } else {
+        if (eval_block == 256) fim_eval_kernel<T, 256, false><<<grid_eval / 2, 256, 0, st>>>(a);
+        else fim_eval_kernel<T, 128, false><<<grid_eval, 128, 0, st>>>(a);
+    }
     if (ev1) cudaEventRecord(ev1, st);
     fim_mark_kernel<T><<<grid_eval, 256, 0, st>>>(a, parity);
     note_launches(4);
@@ -774,7 +788,8 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
     const double Ex = xA * den + num * (xC - xA), Ey = yA * den + num * (yC - yA);
     const double ux = xB * den - Ex, uy = yB * den - Ey;
     const double cross = fabs(yB * Ex - xB * Ey);
-    const double v = (double)tB + R.h * cross * rsqrt(phase_L<double>(R, ux, uy));
+    const double L = R.vtab ? phase_L<double, true>(R, ux, uy) : phase_L<double, false>(R, ux, uy);
+    const double v = (double)tB + R.h * cross * rsqrt(L);
     rec = r;
     return v > (double)tC ? v : alf_inf<double>();
 }

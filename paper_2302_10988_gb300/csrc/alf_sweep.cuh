@@ -78,7 +78,7 @@ ALF_D unsigned warp_seed_square(const WarpGrid<T>& g, int ci, int cj, int r)
 
 // rounds of one grid to its fixed point; returns the evaluations, writes the rounds taken, false when the
 // round cap was reached
-template <typename T>
+template <typename T, bool VT = false>
 ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -142,7 +142,7 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
                 for (int c = 0; c < 4; ++c) R.fb[c] *= g.scale;
             }
             int rc;
-            const T v = local_F<T>(nb, (int)n, nx, R, rc);
+            const T v = local_F<T, VT>(nb, (int)n, nx, R, rc);
             if (g.rec) g.rec[n] = (uint8_t)rc;
             if (!same_bits(v, old)) tf[n] = v;
             g.ov[e] = old;
@@ -265,7 +265,7 @@ ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaS
     return nact;
 }
 
-template <typename T, int NT>
+template <typename T, int NT, bool VT = false>
 ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds,
                      CtaSweepShared& sh)
 {
@@ -342,7 +342,7 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                 for (int c = 0; c < 4; ++c) R.fb[c] *= g.scale;
             }
             int rc;
-            const T v = local_F<T>(nb, (int)n, nx, R, rc);
+            const T v = local_F<T, VT>(nb, (int)n, nx, R, rc);
             if (g.rec) g.rec[n] = (uint8_t)rc;
             if (!same_bits(v, old)) tf[n] = v;
             g.ov[e] = old;
