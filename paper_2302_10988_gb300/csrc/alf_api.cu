@@ -729,7 +729,8 @@ alf_status alf_check64(alf_plan* p, const double* theta, const void* times, cons
     ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
                                       p->opt.group_model, p->d_regions64, st, p->d_vtab64));
     ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
-                                 records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st));
+                                 records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st,
+                                 p->opt.velocity_table));
     return ALF_OK;
 }
 

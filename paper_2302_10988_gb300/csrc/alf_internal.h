@@ -94,7 +94,7 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
                            const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
                            const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
-                           cudaStream_t st);
+                           cudaStream_t st, int vtable = 0);
 cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
                                  double* out, int n, cudaStream_t st);
 

@@ -760,7 +760,7 @@ ALF_D bool box_frozen(const unsigned* bits, int box, const FieldDesc& fd, int i,
 // next best's when it is not usable) is evaluated in FP64.  Triangle metrics
 // and the fallback, which need FP64 arithmetic, are evaluated only when no
 // square is usable.  All decisions are the ones an all-FP64 evaluation makes.
-template <typename T>
+template <typename T, bool VT>
 ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R, int& rec)
 {
     int xA = 0, yA = 0, xB = 0, yB = 0, xC = 0, yC = 0, r = 255;
@@ -788,13 +788,12 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
     const double Ex = xA * den + num * (xC - xA), Ey = yA * den + num * (yC - yA);
     const double ux = xB * den - Ex, uy = yB * den - Ey;
     const double cross = fabs(yB * Ex - xB * Ey);
-    const double L = R.vtab ? phase_L<double, true>(R, ux, uy) : phase_L<double, false>(R, ux, uy);
-    const double v = (double)tB + R.h * cross * rsqrt(L);
+    const double v = (double)tB + R.h * cross * rsqrt(phase_L<double, VT>(R, ux, uy));
     rec = r;
     return v > (double)tC ? v : alf_inf<double>();
 }
 
-template <typename T>
+template <typename T, bool VT>
 __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint16_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
                                const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips)
@@ -874,7 +873,7 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
             }
             cand &= ~(1u << bp);
             int r;
-            const double v = check_pair_time<T>(bp, t, R, r);
+            const double v = check_pair_time<T, VT>(bp, t, R, r);
             if (v < inf64) {
                 F = v;
                 rec = r;
@@ -898,7 +897,7 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
             }
             cand &= ~(1u << bp);
             int r;
-            const double v = check_pair_time<T>(bp, t, R, r);
+            const double v = check_pair_time<T, VT>(bp, t, R, r);
             if (v < inf64) {
                 F = v;
                 rec = r;
@@ -944,21 +943,29 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
                            const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
                            const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
-                           cudaStream_t st)
+                           cudaStream_t st, int vtable)
 {
     cudaError_t e = cudaMemsetAsync(max_rel, 0, sizeof(double) * nfields, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(n_flips, 0, sizeof(int32_t) * nfields, st);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, grid_ctas);
-    if (precision == ALF_FP64)
-        check64_kernel<double><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map,
-                                                     (const RegionP<double>*)regions64, nregions, records,
-                                                     frozen_bits, box, max_rel, n_flips);
-    else
-        check64_kernel<float><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map,
-                                                    (const RegionP<double>*)regions64, nregions, records,
-                                                    frozen_bits, box, max_rel, n_flips);
+    const RegionP<double>* R64 = (const RegionP<double>*)regions64;
+    if (precision == ALF_FP64) {
+        if (vtable)
+            check64_kernel<double, true><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map, R64,
+                                                               nregions, records, frozen_bits, box, max_rel, n_flips);
+        else
+            check64_kernel<double, false><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map, R64,
+                                                                nregions, records, frozen_bits, box, max_rel, n_flips);
+    } else {
+        if (vtable)
+            check64_kernel<float, true><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map, R64,
+                                                              nregions, records, frozen_bits, box, max_rel, n_flips);
+        else
+            check64_kernel<float, false><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map, R64,
+                                                               nregions, records, frozen_bits, box, max_rel, n_flips);
+    }
     note_launches(1);
     return cudaGetLastError();
 }
