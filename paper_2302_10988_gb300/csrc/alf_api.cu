@@ -69,12 +69,6 @@ bool material_to_matd(const alf_material& m, MatD* out)
     return true;
 }
 
-size_t next_pow2(size_t v)
-{
-    size_t p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -25,22 +25,11 @@ unsigned long long launches_so_far() { return g_launches.load(); }
 // ---------------------------------------------------------------------------
 // small device helpers
 // ---------------------------------------------------------------------------
-ALF_D unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 ALF_D unsigned ld_volatile(const unsigned* p) { return *reinterpret_cast<const volatile unsigned*>(p); }
 
 ALF_D void set_error(QueueState* q, unsigned code) { atomicCAS(&q->error, 0u, code); }
 
-template <typename T>
-ALF_D T load_cg(const T* p)
-{
-    return __ldcg(p);
-}
 
 // ---------------------------------------------------------------------------
 // prep_regions
