@@ -318,6 +318,26 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
     T u = inf;
     int urec = 255;
     int k = -1;
+    {
+        // Before the first pair is available U is a fallback value, never below gmin (the least fallback
+        // value over every slot that is or becomes known), and c() grows with its argument: when
+        // c(gmin) - 1 reaches the first pair's step, no step before it can stop, so the walk starts there.
+        const unsigned ev_pair = ev_sq | ev_tr;
+        if (ev_pair > 1u) {  // the first pair is not available from the start
+            T gmin = inf;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+                const T gq = t[q] + ((q >= 8) ? T(2) * R.fb[scls(q)] : R.fb[scls(q)]);
+                if (rk[q] < 64 && gq < gmin) gmin = gq;
+            }
+            int cmin = 0;
+#pragma unroll
+            for (int q = 0; q < 12; ++q)
+                cmin += (((cd >> q) & 1u) && (sord(q) < 12 ? t[q] <= gmin : t[q] < gmin)) ? 1 : 0;
+            const int first = __ffs((int)ev_pair) - 2;
+            if (cmin - 1 >= first) k = first;
+        }
+    }
 #pragma unroll 1
     for (int guard = 0; guard < 14; ++guard) {
         T bm = inf, bv = inf;
