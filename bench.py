@@ -39,12 +39,14 @@ sys.path.insert(0, ROOT)
 METRIC = "travel-time nodes/s (sources x models x nodes), batched FP32"
 WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 regions, FP32; "
             "step = solve + FP64 check + 32 rays/source + adjoint gradient")
-# algorithmic FP32-pipe operations of one evaluation of the local operator (derivation in the design doc)
+# algorithmic FP32-pipe operations of one evaluation of the local operator: 12 absolute values and masks,
+# 66 rank compares, 48 feasibility compares, ~181 for the stencil times and metrics of 4.9 feasible pairs
+# (37 each) and ~320 for the walk (2-3 change steps of ~100)
 OPS_PER_EVAL = 627.0
-# DRAM bytes (read + write) per evaluation of the field-resident sweep kernel, from an ncu capture of
-# a 2,560-field solve (profiles/fim_warp_kernel_weld_batch_80x32.md); scaled to a launch by its
-# evaluations.  Set to None when that kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": None}  # the kernel changed since the last capture
+# DRAM bytes (read + write) per evaluation of each sweep kernel, from one ncu capture of a 2,560-field
+# solve (80 weld samples x 32 sources); scaled to a launch by its evaluations.  None for a kernel that
+# changed since its capture.
+TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel": None}
 SMS, FP32_LANES = 152, 128
 
 
@@ -61,7 +63,7 @@ def _args():
                          "one step, a short summary line (for ncu)")
     ap.add_argument("--profile-stages", default="all", choices=["all", "solve"],
                     help="profiling run: the whole step, or the travel-time solve alone")
-    ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2, 3],
                     help="profiling run: sweep schedule (0: the library's choice)")
     return ap.parse_args()
 
@@ -351,7 +353,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fields": P.nfields, "nodes_per_step": P.total_nodes,
                    "rays_per_step": P.nfields * P.nrec, "band_cells": P.options.band_cells,
-                   "sweep": "one warp per field" if P.options.sweep == 2 else "lockstep rounds over all fields",
+                   "sweep": {1: "lockstep rounds over all fields", 2: "one warp per field",
+                             3: "one CTA per field"}[P.options.sweep],
                    "l2": "inputs larger than L2 (3.6 GB of fields), no flush"},
         "stage_ms": stage, "evaluations_per_node": evals_per_node,
         "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},
