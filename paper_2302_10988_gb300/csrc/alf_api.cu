@@ -150,6 +150,14 @@ alf_status run_sweep(alf_plan* p, const FimLaunch& a, cudaStream_t st)
 
 }  // namespace
 
+// CTA-per-field sweep shape: threads per field and a grid of as many CTAs as fit on the SMs at once
+static void set_cta_threads(alf_plan* p, int threads, int precision, bool vtable)
+{
+    p->cta_threads = threads;
+    const int c = fim_cta_ctas_per_sm(precision, p->cta_words, vtable, threads);
+    p->cta_grid = std::max(1, c) * p->ctx->nsm;
+}
+
 extern "C" {
 
 void alf_default_options(alf_options* o)
@@ -299,6 +307,8 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (opt.ray_family < 0 || opt.ray_family > 5) return fail(ctx, ALF_ERR_INVALID_ARG, "ray_family must be in 0..5");
     if (opt.velocity_table != 0 && opt.velocity_table != 1)
         return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table must be 0 or 1");
+    if (opt.cta_threads != 0 && opt.cta_threads != 64 && opt.cta_threads != 128 && opt.cta_threads != 256)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 64, 128 or 256");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
@@ -414,10 +424,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // CTA-per-field sweep: shared bitmap when the largest field's fits in 64 KB, else global bitmaps
     p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
     if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
-    {
-        const int c = fim_cta_ctas_per_sm(opt.precision, p->cta_words, opt.velocity_table != 0);
-        p->cta_grid = std::max(1, c) * ctx->nsm;
-    }
+    set_cta_threads(p, opt.cta_threads ? opt.cta_threads : 256, opt.precision, opt.velocity_table != 0);
     p->sweep_mode = opt.sweep != 0 ? opt.sweep
                     : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 3;
     // launch shapes of the sweep: one warp per field for the per-field steps, a
@@ -603,6 +610,7 @@ alf_status alf_plan_options(const alf_plan* p, alf_options* out)
     if (!p || !out) return ALF_ERR_INVALID_ARG;
     *out = p->opt;
     out->sweep = p->sweep_mode;
+    out->cta_threads = p->cta_threads;
     return ALF_OK;
 }
 
@@ -692,7 +700,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
         }
         if (timing) ALF_CUDA(ctx, cudaEventRecord(p->ev[0], st));
         if (p->sweep_mode == 2) ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
-        else ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, st));
+        else ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, p->cta_threads, st));
         if (timing) {
             ALF_CUDA(ctx, cudaEventRecord(p->ev[1], st));
             ALF_CUDA(ctx, cudaEventSynchronize(p->ev[1]));
@@ -913,15 +921,19 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     std::vector<Cand> cands;
     const bool try1 = p->opt.sweep == 0 || p->opt.sweep == 1;
     const bool try2 = (p->opt.sweep == 0 || p->opt.sweep == 2) && p->warp_grid > 0;
+    // (block: the evaluation block of the lockstep rounds, the threads of one field's CTA for sweep 3)
     if (try1)
         for (double band : {2.0, 3.0, 4.0, 6.0})
             for (int blk : {128, 256}) cands.push_back({1, band, blk});
     if (try2)
         for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block});
     if (p->opt.sweep == 0 || p->opt.sweep == 3)
-        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({3, band, p->eval_block});
+        for (double band : {1.0, 2.0, 3.0, 4.0})
+            for (int nt : {64, 128, 256})
+                if (p->opt.cta_threads == 0 || p->opt.cta_threads == nt) cands.push_back({3, band, nt});
     double best_ms = 1e30, best_band = p->opt.band_cells;
-    int best_block = p->eval_block, best_mode = p->sweep_mode;
+    const int eval_block0 = p->eval_block;
+    int best_block = p->sweep_mode == 3 ? p->cta_threads : p->eval_block, best_mode = p->sweep_mode;
     cudaEvent_t e0, e1;
     ALF_CUDA(ctx, cudaEventCreate(&e0));
     ALF_CUDA(ctx, cudaEventCreate(&e1));
@@ -929,7 +941,8 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     p->opt.time_kernels = 0;
     for (const Cand& c : cands) {
         p->opt.band_cells = c.band;
-        p->eval_block = c.block;
+        p->eval_block = c.mode == 1 ? c.block : eval_block0;
+        if (c.mode == 3) set_cta_threads(p, c.block, p->opt.precision, p->opt.velocity_table != 0);
         p->sweep_mode = c.mode;
         if (p->chunk_graph) {
             cudaGraphExecDestroy(p->chunk_graph);
@@ -958,7 +971,8 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->opt.band_cells = best_band;
-    p->eval_block = best_block;
+    p->eval_block = best_mode == 1 ? best_block : eval_block0;
+    set_cta_threads(p, best_mode == 3 ? best_block : (p->opt.cta_threads ? p->opt.cta_threads : 256), p->opt.precision, p->opt.velocity_table != 0);
     p->sweep_mode = best_mode;
     p->opt.time_kernels = keep_timing;
     if (p->chunk_graph) {

@@ -86,8 +86,8 @@ cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* o
 int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp, bool vt);  // 0: does not fit
 // field-resident sweep by a CTA per field (few large fields); bitmaps of up to smem_words words in shared memory
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           cudaStream_t st);
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt);
+                           int threads, cudaStream_t st);
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt, int threads);
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -247,6 +247,7 @@ struct alf_plan {
     int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field, 3: one CTA per field
     unsigned cta_words = 0;         // shared bitmap words of the CTA-per-field sweep
     int cta_grid = 0;
+    int cta_threads = 256;          // threads of one field's CTA: 64, 128 or 256
     unsigned warp_words = 0;        // dirty-bitmap words of the largest field
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size

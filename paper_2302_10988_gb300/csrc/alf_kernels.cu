@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
 // Field-resident sweep by a whole CTA (few large fields): the same rounds, block barriers between the
 // steps.  The dirty bitmap is in shared memory when the field's fits, else in the field's global bitmap.
 template <typename T, int NT, bool VT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
     fim_cta_kernel(FimLaunch a, const unsigned* order, unsigned smem_words)
 {
     extern __shared__ unsigned s_cbm[];
@@ -540,55 +540,78 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
 }
 
-#define ALF_CTA_THREADS 256
-
-template <typename T, bool VT>
+// CTA sizes of the CTA-per-field sweep: 64, 128 or 256 threads (2, 4 or 8 warps on one field).  Fewer
+// warps per field put more fields on an SM at once; more warps finish a large field sooner.
+template <typename T, int NT, bool VT>
 static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
 {
     *smem = (size_t)smem_words * sizeof(unsigned);
     if (*smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fim_cta_kernel<T, ALF_CTA_THREADS, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)*smem);
+    return cudaFuncSetAttribute(fim_cta_kernel<T, NT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
 }
 
-template <typename T, bool VT>
+template <typename T, int NT, bool VT>
 static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                              cudaStream_t st)
 {
     size_t smem = 0;
-    cudaError_t e = fim_cta_smem<T, VT>(smem_words, &smem);
+    cudaError_t e = fim_cta_smem<T, NT, VT>(smem_words, &smem);
     if (e != cudaSuccess) return e;
-    fim_cta_kernel<T, ALF_CTA_THREADS, VT><<<grid, ALF_CTA_THREADS, smem, st>>>(a, order, smem_words);
+    fim_cta_kernel<T, NT, VT><<<grid, NT, smem, st>>>(a, order, smem_words);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           cudaStream_t st)
+template <typename T, bool VT>
+static cudaError_t fim_cta_nt(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid, int nt,
+                              cudaStream_t st)
 {
-    if (a.vtable)
-        return precision == ALF_FP64 ? fim_cta_t<double, true>(a, order, smem_words, grid, st)
-                                     : fim_cta_t<float, true>(a, order, smem_words, grid, st);
-    return precision == ALF_FP64 ? fim_cta_t<double, false>(a, order, smem_words, grid, st)
-                                 : fim_cta_t<float, false>(a, order, smem_words, grid, st);
+    switch (nt) {
+    case 64: return fim_cta_t<T, 64, VT>(a, order, smem_words, grid, st);
+    case 128: return fim_cta_t<T, 128, VT>(a, order, smem_words, grid, st);
+    case 256: return fim_cta_t<T, 256, VT>(a, order, smem_words, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-template <typename T, bool VT>
+cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                           int threads, cudaStream_t st)
+{
+    if (a.vtable)
+        return precision == ALF_FP64 ? fim_cta_nt<double, true>(a, order, smem_words, grid, threads, st)
+                                     : fim_cta_nt<float, true>(a, order, smem_words, grid, threads, st);
+    return precision == ALF_FP64 ? fim_cta_nt<double, false>(a, order, smem_words, grid, threads, st)
+                                 : fim_cta_nt<float, false>(a, order, smem_words, grid, threads, st);
+}
+
+template <typename T, int NT, bool VT>
 static int fim_cta_occ(unsigned smem_words)
 {
     size_t smem = 0;
-    if (fim_cta_smem<T, VT>(smem_words, &smem) != cudaSuccess) return 0;
+    if (fim_cta_smem<T, NT, VT>(smem_words, &smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, ALF_CTA_THREADS, VT>, ALF_CTA_THREADS,
-                                                      smem) != cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, NT, VT>, NT, smem) != cudaSuccess) return 0;
     return n;
 }
 
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt)
+template <typename T, bool VT>
+static int fim_cta_occ_nt(unsigned smem_words, int nt)
 {
-    if (vt) return precision == ALF_FP64 ? fim_cta_occ<double, true>(smem_words) : fim_cta_occ<float, true>(smem_words);
-    return precision == ALF_FP64 ? fim_cta_occ<double, false>(smem_words) : fim_cta_occ<float, false>(smem_words);
+    switch (nt) {
+    case 64: return fim_cta_occ<T, 64, VT>(smem_words);
+    case 128: return fim_cta_occ<T, 128, VT>(smem_words);
+    case 256: return fim_cta_occ<T, 256, VT>(smem_words);
+    default: return 0;
+    }
+}
+
+int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt, int threads)
+{
+    if (vt)
+        return precision == ALF_FP64 ? fim_cta_occ_nt<double, true>(smem_words, threads)
+                                     : fim_cta_occ_nt<float, true>(smem_words, threads);
+    return precision == ALF_FP64 ? fim_cta_occ_nt<double, false>(smem_words, threads)
+                                 : fim_cta_occ_nt<float, false>(smem_words, threads);
 }
 
 // dynamic shared memory of the field-resident sweep: one dirty bitmap per warp

@@ -152,6 +152,9 @@ def test_host_validation_errors(api):
     with pytest.raises(B.AlfError) as e:
         api.Plan(wl, precision="fp64", sweep=5)
     assert e.value.code == 1
+    with pytest.raises(B.AlfError) as e:
+        api.Plan(wl, precision="fp64", sweep=3, cta_threads=96)
+    assert e.value.code == 1
 
 
 def test_graph_stream_and_timing(api, oracle):
@@ -176,6 +179,9 @@ def test_graph_stream_and_timing(api, oracle):
     assert (t3 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
     opt = Pt.autotune(th)
     assert opt.band_cells in (1.0, 2.0, 3.0, 4.0, 6.0) and opt.sweep in (1, 2, 3)
+    assert opt.cta_threads in (64, 128, 256)
+    t4, _ = Pt.solve(th)
+    assert (t4 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
 
 
 def test_sweep_schedules_agree(api, oracle):
@@ -187,6 +193,10 @@ def test_sweep_schedules_agree(api, oracle):
     P3, _, t3, _, rec3 = _solve(api, wl, "fp64", sweep=3)
     assert torch.equal(t1, t2) and torch.equal(t1, t3)
     assert torch.equal(rec1, rec2) and torch.equal(rec1, rec3)
+    for nt in (64, 128):  # fewer warps on each field's CTA
+        Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_threads=nt)
+        assert Pn.options.cta_threads == nt
+        assert torch.equal(t1, tn) and torch.equal(rec1, recn)
     for b, s in ((0, 0), (3, 2), (5, 3)):
         tau, orec, fr, M = oracle_field(oracle, wl, b, s)
         assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
