@@ -380,6 +380,7 @@ def main():
             P1 = api.Plan(wl1, precision=prec, device=local)
             th1 = P1.theta_tensor()
             t1 = P1.new_times()
+            P1.autotune(th1, t1)
             P1.solve(th1, times=t1)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -389,6 +390,8 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             plain[prec] = P1.total_nodes / (e0.elapsed_time(e1) / 3 * 1e-3)
+            plain[prec + "_schedule"] = {"sweep": P1.options.sweep, "band_cells": P1.options.band_cells,
+                                         "cta_threads": P1.options.cta_threads}
             del P1, t1
         line["plain_nodes_per_s"] = plain
         # large single medium: 2048 x 2048, 64 sources, 4096 receivers per source
@@ -409,7 +412,8 @@ def main():
         line["large_medium"] = {"config": "2048 x 2048, 0.1 mm, 100 x 100 regions, 64 sources x 4096 receivers, FP32",
                                 "nodes_per_s": PL.total_nodes / (e0.elapsed_time(e1) * 1e-3),
                                 "rays_per_s": PL.nfields * PL.nrec / (e1.elapsed_time(e2) * 1e-3),
-                                "sweep": PL.options.sweep, "status": PL.status()}
+                                "sweep": PL.options.sweep, "cta_threads": PL.options.cta_threads,
+                                "status": PL.status()}
         del PL, tL
         # gradient: 256 samples x 32 sources on 200 x 200, forward (records) + adjoint
         wl3, truth = W.weld_adjoint()

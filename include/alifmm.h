@@ -126,8 +126,9 @@ typedef struct {
                                of phase speeds at integer degrees (Sec. 3; Table 2 compares it with solving
                                the Christoffel matrix at run time, 0, the default).  Group speeds (source
                                initialisation, fallback, rays) are unchanged.  alf_backward refuses it. */
-    int cta_threads;        /* sweep 3: threads of the CTA that owns a field, 64, 128 or 256 (2, 4 or 8
-                               warps); 0 = 256, the default.  alf_plan_autotune chooses it among the three. */
+    int cta_threads;        /* sweep 3: threads of the CTA that owns a field, 64, 128, 256 or 512 (2 to 16
+                               warps); 0 = choose (default): 512 for FP32 batches with no more fields than
+                               SMs, else 256.  alf_plan_autotune chooses it among the four. */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */

@@ -307,8 +307,9 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (opt.ray_family < 0 || opt.ray_family > 5) return fail(ctx, ALF_ERR_INVALID_ARG, "ray_family must be in 0..5");
     if (opt.velocity_table != 0 && opt.velocity_table != 1)
         return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table must be 0 or 1");
-    if (opt.cta_threads != 0 && opt.cta_threads != 64 && opt.cta_threads != 128 && opt.cta_threads != 256)
-        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 64, 128 or 256");
+    if (opt.cta_threads != 0 && opt.cta_threads != 64 && opt.cta_threads != 128 && opt.cta_threads != 256 &&
+        opt.cta_threads != 512)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 64, 128, 256 or 512");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
@@ -424,7 +425,9 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // CTA-per-field sweep: shared bitmap when the largest field's fits in 64 KB, else global bitmaps
     p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
     if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
-    set_cta_threads(p, opt.cta_threads ? opt.cta_threads : 256, opt.precision, opt.velocity_table != 0);
+    // default: a whole SM per field when the fields do not outnumber the SMs (FP32), else 8 warps per field
+    p->cta_default = (opt.precision == ALF_FP32 && p->nfields <= ctx->nsm) ? 512 : 256;
+    set_cta_threads(p, opt.cta_threads ? opt.cta_threads : p->cta_default, opt.precision, opt.velocity_table != 0);
     p->sweep_mode = opt.sweep != 0 ? opt.sweep
                     : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 3;
     // launch shapes of the sweep: one warp per field for the per-field steps, a
@@ -929,7 +932,7 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
         for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block});
     if (p->opt.sweep == 0 || p->opt.sweep == 3)
         for (double band : {1.0, 2.0, 3.0, 4.0})
-            for (int nt : {64, 128, 256})
+            for (int nt : {64, 128, 256, 512})
                 if (p->opt.cta_threads == 0 || p->opt.cta_threads == nt) cands.push_back({3, band, nt});
     double best_ms = 1e30, best_band = p->opt.band_cells;
     const int eval_block0 = p->eval_block;
@@ -972,7 +975,7 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     cudaEventDestroy(e1);
     p->opt.band_cells = best_band;
     p->eval_block = best_mode == 1 ? best_block : eval_block0;
-    set_cta_threads(p, best_mode == 3 ? best_block : (p->opt.cta_threads ? p->opt.cta_threads : 256), p->opt.precision, p->opt.velocity_table != 0);
+    set_cta_threads(p, best_mode == 3 ? best_block : (p->opt.cta_threads ? p->opt.cta_threads : p->cta_default), p->opt.precision, p->opt.velocity_table != 0);
     p->sweep_mode = best_mode;
     p->opt.time_kernels = keep_timing;
     if (p->chunk_graph) {

@@ -247,7 +247,8 @@ struct alf_plan {
     int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field, 3: one CTA per field
     unsigned cta_words = 0;         // shared bitmap words of the CTA-per-field sweep
     int cta_grid = 0;
-    int cta_threads = 256;          // threads of one field's CTA: 64, 128 or 256
+    int cta_threads = 256;          // threads of one field's CTA: 64, 128, 256 or 512
+    int cta_default = 256;          // the plan's choice when the options leave it open
     unsigned warp_words = 0;        // dirty-bitmap words of the largest field
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size

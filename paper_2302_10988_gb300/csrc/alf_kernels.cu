@@ -540,8 +540,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
     }
 }
 
-// CTA sizes of the CTA-per-field sweep: 64, 128 or 256 threads (2, 4 or 8 warps on one field).  Fewer
-// warps per field put more fields on an SM at once; more warps finish a large field sooner.
+// CTA sizes of the CTA-per-field sweep: 64, 128, 256 or 512 threads (2 to 16 warps on one field).  Fewer
+// warps per field put more fields on an SM at once; more warps finish a large field sooner (512: a whole
+// SM's FP32 register file for one field, for batches with no more fields than SMs).
 template <typename T, int NT, bool VT>
 static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
 {
@@ -570,6 +571,7 @@ static cudaError_t fim_cta_nt(const FimLaunch& a, const unsigned* order, unsigne
     case 64: return fim_cta_t<T, 64, VT>(a, order, smem_words, grid, st);
     case 128: return fim_cta_t<T, 128, VT>(a, order, smem_words, grid, st);
     case 256: return fim_cta_t<T, 256, VT>(a, order, smem_words, grid, st);
+    case 512: return fim_cta_t<T, 512, VT>(a, order, smem_words, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -601,6 +603,7 @@ static int fim_cta_occ_nt(unsigned smem_words, int nt)
     case 64: return fim_cta_occ<T, 64, VT>(smem_words);
     case 128: return fim_cta_occ<T, 128, VT>(smem_words);
     case 256: return fim_cta_occ<T, 256, VT>(smem_words);
+    case 512: return fim_cta_occ<T, 512, VT>(smem_words);
     default: return 0;
     }
 }
