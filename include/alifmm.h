@@ -129,6 +129,9 @@ typedef struct {
     int cta_threads;        /* sweep 3: threads of the CTA that owns a field, 64, 128, 256 or 512 (2 to 16
                                warps); 0 = choose (default): 512 for FP32 batches with no more fields than
                                SMs, else 256.  alf_plan_autotune chooses it among the four. */
+    int cta_cluster;        /* sweep 3: CTAs of 512 threads that share one field as a thread-block cluster on
+                               as many SMs, 1, 2, 4 or 8; 0 = choose (default): for FP32 batches with no more
+                               fields than SMs, the largest that keeps fields x cluster <= SMs, else 1 */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */

@@ -42,7 +42,7 @@ class Plan:
     Keyword options map to ``alf_options`` fields (precision "fp32"/"fp64",
     group "paper"/"exact", init_mode, init_radius, n_levels, level_density, level_radius,
     plane_step, ray_halfwidth, ray_family, stop_radius, max_ray_points, max_rounds, sweep, keep_records,
-    band_cells, use_graph, time_kernels, velocity_table, cta_threads); array fields take a sequence of 4 ints."""
+    band_cells, use_graph, time_kernels, velocity_table, cta_threads, cta_cluster); array fields take a sequence of 4 ints."""
 
     def __init__(self, wl, precision="fp32", group="paper", device=0, **opts):
         self.wl = wl

@@ -150,12 +150,15 @@ alf_status run_sweep(alf_plan* p, const FimLaunch& a, cudaStream_t st)
 
 }  // namespace
 
-// CTA-per-field sweep shape: threads per field and a grid of as many CTAs as fit on the SMs at once
-static void set_cta_threads(alf_plan* p, int threads, int precision, bool vtable)
+// CTA-per-field sweep shape: threads per CTA, CTAs per field (a cluster) and a grid of as many CTAs as are
+// resident at once; a cluster that cannot be resident falls back to one CTA per field
+static void set_cta_shape(alf_plan* p, int threads, int cluster, int precision, bool vtable)
 {
-    p->cta_threads = threads;
-    const int c = fim_cta_ctas_per_sm(precision, p->cta_words, vtable, threads);
-    p->cta_grid = std::max(1, c) * p->ctx->nsm;
+    if (cluster > 1 && fim_cta_grid(precision, p->cta_words, vtable, 512, cluster, p->ctx->nsm) < cluster) cluster = 1;
+    p->cta_threads = cluster > 1 ? 512 : threads;
+    p->cta_cluster = cluster;
+    p->cta_grid = std::max(p->cta_cluster,
+                           fim_cta_grid(precision, p->cta_words, vtable, p->cta_threads, cluster, p->ctx->nsm));
 }
 
 extern "C" {
@@ -310,6 +313,11 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (opt.cta_threads != 0 && opt.cta_threads != 64 && opt.cta_threads != 128 && opt.cta_threads != 256 &&
         opt.cta_threads != 512)
         return fail(ctx, ALF_ERR_INVALID_ARG, "cta_threads must be 0, 64, 128, 256 or 512");
+    if (opt.cta_cluster != 0 && opt.cta_cluster != 1 && opt.cta_cluster != 2 && opt.cta_cluster != 4 &&
+        opt.cta_cluster != 8)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_cluster must be 0, 1, 2, 4 or 8");
+    if (opt.cta_cluster > 1 && opt.cta_threads != 0 && opt.cta_threads != 512)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "cta_cluster > 1 needs cta_threads 512 (or 0)");
     if (opt.max_rounds < 1) return fail(ctx, ALF_ERR_INVALID_ARG, "max_rounds must be >= 1");
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
@@ -425,9 +433,17 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // CTA-per-field sweep: shared bitmap when the largest field's fits in 64 KB, else global bitmaps
     p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
     if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
-    // default: a whole SM per field when the fields do not outnumber the SMs (FP32), else 8 warps per field
+    // default: a whole SM per field when the fields do not outnumber the SMs (FP32), and a cluster of 2, 4 or
+    // 8 SMs per field when they leave that many SMs per field idle; else 8 warps per field
     p->cta_default = (opt.precision == ALF_FP32 && p->nfields <= ctx->nsm) ? 512 : 256;
-    set_cta_threads(p, opt.cta_threads ? opt.cta_threads : p->cta_default, opt.precision, opt.velocity_table != 0);
+    p->cluster_default = 1;
+    if (p->cta_default == 512)
+        for (int cs : {2, 4, 8})
+            if ((long long)p->nfields * cs <= ctx->nsm) p->cluster_default = cs;
+    {
+        const int cs = opt.cta_cluster ? opt.cta_cluster : (opt.cta_threads && opt.cta_threads != 512 ? 1 : p->cluster_default);
+        set_cta_shape(p, opt.cta_threads ? opt.cta_threads : p->cta_default, cs, opt.precision, opt.velocity_table != 0);
+    }
     p->sweep_mode = opt.sweep != 0 ? opt.sweep
                     : (p->warp_grid > 0 && p->nfields >= p->warp_grid * ALF_SWEEP_WARPS) ? 2 : 3;
     // launch shapes of the sweep: one warp per field for the per-field steps, a
@@ -614,6 +630,7 @@ alf_status alf_plan_options(const alf_plan* p, alf_options* out)
     *out = p->opt;
     out->sweep = p->sweep_mode;
     out->cta_threads = p->cta_threads;
+    out->cta_cluster = p->cta_cluster;
     return ALF_OK;
 }
 
@@ -703,7 +720,9 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
         }
         if (timing) ALF_CUDA(ctx, cudaEventRecord(p->ev[0], st));
         if (p->sweep_mode == 2) ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
-        else ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, p->cta_threads, st));
+        else
+            ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, p->cta_threads, p->cta_cluster,
+                                         st));
         if (timing) {
             ALF_CUDA(ctx, cudaEventRecord(p->ev[1], st));
             ALF_CUDA(ctx, cudaEventSynchronize(p->ev[1]));
@@ -920,6 +939,7 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
         int mode;
         double band;
         int block;
+        int cluster;
     };
     std::vector<Cand> cands;
     const bool try1 = p->opt.sweep == 0 || p->opt.sweep == 1;
@@ -927,16 +947,24 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     // (block: the evaluation block of the lockstep rounds, the threads of one field's CTA for sweep 3)
     if (try1)
         for (double band : {2.0, 3.0, 4.0, 6.0})
-            for (int blk : {128, 256}) cands.push_back({1, band, blk});
+            for (int blk : {128, 256}) cands.push_back({1, band, blk, 1});
     if (try2)
-        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block});
+        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block, 1});
     if (p->opt.sweep == 0 || p->opt.sweep == 3)
-        for (double band : {1.0, 2.0, 3.0, 4.0})
-            for (int nt : {64, 128, 256, 512})
-                if (p->opt.cta_threads == 0 || p->opt.cta_threads == nt) cands.push_back({3, band, nt});
+        for (double band : {1.0, 2.0, 3.0, 4.0}) {
+            if (p->opt.cta_cluster <= 1)
+                for (int nt : {64, 128, 256, 512})
+                    if (p->opt.cta_threads == 0 || p->opt.cta_threads == nt) cands.push_back({3, band, nt, 1});
+            // clusters only where fields leave SMs idle
+            for (int cs : {2, 4, 8})
+                if ((p->opt.cta_cluster == 0 || p->opt.cta_cluster == cs) &&
+                    (p->opt.cta_threads == 0 || p->opt.cta_threads == 512) && (long long)p->nfields * cs <= 2 * p->ctx->nsm)
+                    cands.push_back({3, band, 512, cs});
+        }
     double best_ms = 1e30, best_band = p->opt.band_cells;
     const int eval_block0 = p->eval_block;
     int best_block = p->sweep_mode == 3 ? p->cta_threads : p->eval_block, best_mode = p->sweep_mode;
+    int best_cluster = p->cta_cluster;
     cudaEvent_t e0, e1;
     ALF_CUDA(ctx, cudaEventCreate(&e0));
     ALF_CUDA(ctx, cudaEventCreate(&e1));
@@ -945,7 +973,7 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     for (const Cand& c : cands) {
         p->opt.band_cells = c.band;
         p->eval_block = c.mode == 1 ? c.block : eval_block0;
-        if (c.mode == 3) set_cta_threads(p, c.block, p->opt.precision, p->opt.velocity_table != 0);
+        if (c.mode == 3) set_cta_shape(p, c.block, c.cluster, p->opt.precision, p->opt.velocity_table != 0);
         p->sweep_mode = c.mode;
         if (p->chunk_graph) {
             cudaGraphExecDestroy(p->chunk_graph);
@@ -969,13 +997,19 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
             best_band = c.band;
             best_block = c.block;
             best_mode = c.mode;
+            best_cluster = c.cluster;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->opt.band_cells = best_band;
     p->eval_block = best_mode == 1 ? best_block : eval_block0;
-    set_cta_threads(p, best_mode == 3 ? best_block : (p->opt.cta_threads ? p->opt.cta_threads : p->cta_default), p->opt.precision, p->opt.velocity_table != 0);
+    if (best_mode == 3)
+        set_cta_shape(p, best_block, best_cluster, p->opt.precision, p->opt.velocity_table != 0);
+    else
+        set_cta_shape(p, p->opt.cta_threads ? p->opt.cta_threads : p->cta_default,
+                      p->opt.cta_cluster ? p->opt.cta_cluster : p->cluster_default, p->opt.precision,
+                      p->opt.velocity_table != 0);
     p->sweep_mode = best_mode;
     p->opt.time_kernels = keep_timing;
     if (p->chunk_graph) {

@@ -85,9 +85,10 @@ cudaError_t launch_fim_warp(int precision, const FimLaunch& a, const unsigned* o
                             int grid, cudaStream_t st);
 int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp, bool vt);  // 0: does not fit
 // field-resident sweep by a CTA per field (few large fields); bitmaps of up to smem_words words in shared memory
+// (threads: 64..512 per CTA; cluster: 1, or 2 / 4 / 8 CTAs of 512 threads sharing one field)
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           int threads, cudaStream_t st);
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt, int threads);
+                           int threads, int cluster, cudaStream_t st);
+int fim_cta_grid(int precision, unsigned smem_words, bool vt, int threads, int cluster, int nsm);  // CTAs; 0: none
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -249,6 +250,8 @@ struct alf_plan {
     int cta_grid = 0;
     int cta_threads = 256;          // threads of one field's CTA: 64, 128, 256 or 512
     int cta_default = 256;          // the plan's choice when the options leave it open
+    int cta_cluster = 1;            // CTAs (of 512 threads) sharing one field: 1, 2, 4 or 8
+    int cluster_default = 1;
     unsigned warp_words = 0;        // dirty-bitmap words of the largest field
     int warp_grid = 0;              // CTAs of the field-resident sweep (0: not possible)
     unsigned* d_order = nullptr;    // fields by decreasing size

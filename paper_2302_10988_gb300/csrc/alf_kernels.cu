@@ -488,24 +488,29 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
     }
 }
 
-// Field-resident sweep by a whole CTA (few large fields): the same rounds, block barriers between the
-// steps.  The dirty bitmap is in shared memory when the field's fits, else in the field's global bitmap.
-template <typename T, int NT, bool VT>
+// Field-resident sweep by a whole CTA (few large fields), or by a cluster of CS CTAs on CS SMs (fewer fields
+// than SMs): the same rounds, barriers between the steps.  The dirty bitmap is in shared memory (rank 0's)
+// when the field's fits, else in the field's global bitmap.  Rank 0 takes the fields from the queue.
+template <typename T, int NT, bool VT, int CS>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
     fim_cta_kernel(FimLaunch a, const unsigned* order, unsigned smem_words)
 {
     extern __shared__ unsigned s_cbm[];
     __shared__ CtaSweepShared sh;
-    __shared__ unsigned s_f, s_err;
+    __shared__ unsigned s_f[2];  // field index, error code
     const T inf = alf_inf<T>();
+    const unsigned rank = cluster_rank<CS>();
+    CtaSweepShared& S = CS == 1 ? sh : *map_rank(&sh, 0u);
+    const volatile unsigned* const f0 = CS == 1 ? s_f : map_rank(s_f, 0u);
+    unsigned* const bm0 = CS == 1 ? s_cbm : map_rank(s_cbm, 0u);
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_f = atomicAdd(&a.q->head, 1u);
-            s_err = ld_volatile(&a.q->error);
+        if (rank == 0 && threadIdx.x == 0) {
+            s_f[0] = atomicAdd(&a.q->head, 1u);
+            s_f[1] = ld_volatile(&a.q->error);
         }
-        __syncthreads();
-        const unsigned fi = s_f, err = s_err;
-        __syncthreads();
+        sweep_sync<CS>();
+        const unsigned fi = f0[0], err = f0[1];
+        sweep_sync<CS>();
         if (fi >= (unsigned)a.nfields || err != 0u) return;
         const unsigned f = __ldg(order + fi);
         const FieldDesc fd = a.fields[f];
@@ -523,98 +528,151 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
         g.nv = (T*)a.newv + fd.node_off;
         g.rec = a.records ? a.records + fd.node_off : nullptr;
         const unsigned words = (unsigned)((fd.nx * fd.ny + 31) / 32);
-        g.bm = words <= smem_words ? s_cbm : a.bitmap + a.bm_off[f];
+        g.bm = words <= smem_words ? bm0 : a.bitmap + a.bm_off[f];
         g.band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
         g.max_rounds = a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny);
-        const unsigned nact = cta_seed_square<T, NT>(g, fd.si, fd.sj, a.box + 2, sh);
+        const unsigned nact = cta_seed_square<T, NT, CS>(g, fd.si, fd.sj, a.box + 2, S);
         unsigned long long evals = 0ull;
         unsigned rounds = 0u;
-        const bool ok = cta_sweep<T, NT, VT>(g, nact, evals, rounds, sh);
-        if (threadIdx.x == 0) {
+        const bool ok = cta_sweep<T, NT, VT, CS>(g, nact, evals, rounds, S);
+        if (rank == 0 && threadIdx.x == 0) {
             if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
             atomicAdd(&a.q->visits, evals);
             atomicMax(&a.q->rounds, (unsigned long long)rounds);
         }
-        __syncthreads();
+        sweep_sync<CS>();
     }
 }
 
 // CTA sizes of the CTA-per-field sweep: 64, 128, 256 or 512 threads (2 to 16 warps on one field).  Fewer
 // warps per field put more fields on an SM at once; more warps finish a large field sooner (512: a whole
-// SM's FP32 register file for one field, for batches with no more fields than SMs).
-template <typename T, int NT, bool VT>
+// SM's FP32 register file for one field, for batches with no more fields than SMs).  Clusters of 2, 4 or 8
+// 512-thread CTAs spread one field over as many SMs.
+template <typename T, int NT, bool VT, int CS>
 static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
 {
     *smem = (size_t)smem_words * sizeof(unsigned);
     if (*smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fim_cta_kernel<T, NT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    return cudaFuncSetAttribute(fim_cta_kernel<T, NT, VT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)*smem);
 }
 
-template <typename T, int NT, bool VT>
+template <typename T, int NT, bool VT, int CS>
+static cudaLaunchConfig_t cta_config(int grid, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <typename T, int NT, bool VT, int CS>
 static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                              cudaStream_t st)
 {
     size_t smem = 0;
-    cudaError_t e = fim_cta_smem<T, NT, VT>(smem_words, &smem);
+    cudaError_t e = fim_cta_smem<T, NT, VT, CS>(smem_words, &smem);
     if (e != cudaSuccess) return e;
-    fim_cta_kernel<T, NT, VT><<<grid, NT, smem, st>>>(a, order, smem_words);
+    if constexpr (CS == 1) {
+        fim_cta_kernel<T, NT, VT, 1><<<grid, NT, smem, st>>>(a, order, smem_words);
+        e = cudaGetLastError();
+    } else {
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = cta_config<T, NT, VT, CS>(grid, smem, st, attr);
+        e = cudaLaunchKernelEx(&cfg, fim_cta_kernel<T, NT, VT, CS>, a, order, smem_words);
+    }
     note_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T, bool VT>
 static cudaError_t fim_cta_nt(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid, int nt,
-                              cudaStream_t st)
+                              int cs, cudaStream_t st)
 {
-    switch (nt) {
-    case 64: return fim_cta_t<T, 64, VT>(a, order, smem_words, grid, st);
-    case 128: return fim_cta_t<T, 128, VT>(a, order, smem_words, grid, st);
-    case 256: return fim_cta_t<T, 256, VT>(a, order, smem_words, grid, st);
-    case 512: return fim_cta_t<T, 512, VT>(a, order, smem_words, grid, st);
+    if (cs == 1) {
+        switch (nt) {
+        case 64: return fim_cta_t<T, 64, VT, 1>(a, order, smem_words, grid, st);
+        case 128: return fim_cta_t<T, 128, VT, 1>(a, order, smem_words, grid, st);
+        case 256: return fim_cta_t<T, 256, VT, 1>(a, order, smem_words, grid, st);
+        case 512: return fim_cta_t<T, 512, VT, 1>(a, order, smem_words, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (nt != 512) return cudaErrorInvalidValue;
+    switch (cs) {
+    case 2: return fim_cta_t<T, 512, VT, 2>(a, order, smem_words, grid, st);
+    case 4: return fim_cta_t<T, 512, VT, 4>(a, order, smem_words, grid, st);
+    case 8: return fim_cta_t<T, 512, VT, 8>(a, order, smem_words, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           int threads, cudaStream_t st)
+                           int threads, int cluster, cudaStream_t st)
 {
     if (a.vtable)
-        return precision == ALF_FP64 ? fim_cta_nt<double, true>(a, order, smem_words, grid, threads, st)
-                                     : fim_cta_nt<float, true>(a, order, smem_words, grid, threads, st);
-    return precision == ALF_FP64 ? fim_cta_nt<double, false>(a, order, smem_words, grid, threads, st)
-                                 : fim_cta_nt<float, false>(a, order, smem_words, grid, threads, st);
+        return precision == ALF_FP64 ? fim_cta_nt<double, true>(a, order, smem_words, grid, threads, cluster, st)
+                                     : fim_cta_nt<float, true>(a, order, smem_words, grid, threads, cluster, st);
+    return precision == ALF_FP64 ? fim_cta_nt<double, false>(a, order, smem_words, grid, threads, cluster, st)
+                                 : fim_cta_nt<float, false>(a, order, smem_words, grid, threads, cluster, st);
 }
 
-template <typename T, int NT, bool VT>
-static int fim_cta_occ(unsigned smem_words)
+// grid of the CTA-per-field sweep in CTAs: as many CTAs (clusters) as are resident at once; 0: does not fit
+template <typename T, int NT, bool VT, int CS>
+static int fim_cta_occ(unsigned smem_words, int nsm)
 {
     size_t smem = 0;
-    if (fim_cta_smem<T, NT, VT>(smem_words, &smem) != cudaSuccess) return 0;
+    if (fim_cta_smem<T, NT, VT, CS>(smem_words, &smem) != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, NT, VT>, NT, smem) != cudaSuccess) return 0;
-    return n;
+    if constexpr (CS == 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fim_cta_kernel<T, NT, VT, 1>, NT, smem) != cudaSuccess)
+            return 0;
+        return n * nsm;
+    } else {
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = cta_config<T, NT, VT, CS>(CS * nsm, smem, nullptr, attr);
+        if (cudaOccupancyMaxActiveClusters(&n, fim_cta_kernel<T, NT, VT, CS>, &cfg) != cudaSuccess) return 0;
+        return n * CS;
+    }
 }
 
 template <typename T, bool VT>
-static int fim_cta_occ_nt(unsigned smem_words, int nt)
+static int fim_cta_occ_nt(unsigned smem_words, int nt, int cs, int nsm)
 {
-    switch (nt) {
-    case 64: return fim_cta_occ<T, 64, VT>(smem_words);
-    case 128: return fim_cta_occ<T, 128, VT>(smem_words);
-    case 256: return fim_cta_occ<T, 256, VT>(smem_words);
-    case 512: return fim_cta_occ<T, 512, VT>(smem_words);
+    if (cs == 1) {
+        switch (nt) {
+        case 64: return fim_cta_occ<T, 64, VT, 1>(smem_words, nsm);
+        case 128: return fim_cta_occ<T, 128, VT, 1>(smem_words, nsm);
+        case 256: return fim_cta_occ<T, 256, VT, 1>(smem_words, nsm);
+        case 512: return fim_cta_occ<T, 512, VT, 1>(smem_words, nsm);
+        default: return 0;
+        }
+    }
+    if (nt != 512) return 0;
+    switch (cs) {
+    case 2: return fim_cta_occ<T, 512, VT, 2>(smem_words, nsm);
+    case 4: return fim_cta_occ<T, 512, VT, 4>(smem_words, nsm);
+    case 8: return fim_cta_occ<T, 512, VT, 8>(smem_words, nsm);
     default: return 0;
     }
 }
 
-int fim_cta_ctas_per_sm(int precision, unsigned smem_words, bool vt, int threads)
+int fim_cta_grid(int precision, unsigned smem_words, bool vt, int threads, int cluster, int nsm)
 {
     if (vt)
-        return precision == ALF_FP64 ? fim_cta_occ_nt<double, true>(smem_words, threads)
-                                     : fim_cta_occ_nt<float, true>(smem_words, threads);
-    return precision == ALF_FP64 ? fim_cta_occ_nt<double, false>(smem_words, threads)
-                                 : fim_cta_occ_nt<float, false>(smem_words, threads);
+        return precision == ALF_FP64 ? fim_cta_occ_nt<double, true>(smem_words, threads, cluster, nsm)
+                                     : fim_cta_occ_nt<float, true>(smem_words, threads, cluster, nsm);
+    return precision == ALF_FP64 ? fim_cta_occ_nt<double, false>(smem_words, threads, cluster, nsm)
+                                 : fim_cta_occ_nt<float, false>(smem_words, threads, cluster, nsm);
 }
 
 // dynamic shared memory of the field-resident sweep: one dirty bitmap per warp

@@ -209,13 +209,48 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
 
 // ---------------------------------------------------------------------------
 // The same rounds run by a whole CTA of NT threads on one grid (for few, large
-// fields): block barriers between the steps, list slots reserved per warp with
-// shared-memory counters.  The dirty bitmap is in shared or global memory.
+// fields), or by a cluster of CS such CTAs on CS SMs: barriers between the
+// steps, list slots reserved per warp with counters in shared memory (those of
+// the cluster's rank 0 when CS > 1, reached through distributed shared memory).
+// The dirty bitmap is in shared memory (rank 0's) or in global memory.
 // ---------------------------------------------------------------------------
 struct CtaSweepShared {
     unsigned cnt[2];       // evaluation / carried (then marked) list sizes of the round
     unsigned long long kmin[32];
 };
+
+// rank of this CTA in its cluster (0 without clusters)
+template <int CS>
+ALF_D unsigned cluster_rank()
+{
+    if constexpr (CS == 1) {
+        return 0u;
+    } else {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        return r;
+    }
+}
+
+// barrier of the CTA, or of the whole cluster with release / acquire ordering of
+// the global and shared memory operations before and after it
+template <int CS>
+ALF_D void sweep_sync()
+{
+    if constexpr (CS == 1)
+        __syncthreads();
+    else
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// generic address of the same shared-memory object in the cluster's CTA `rank`
+template <typename P>
+ALF_D P* map_rank(P* ptr, unsigned rank)
+{
+    unsigned long long d;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(d) : "l"((unsigned long long)ptr), "r"(rank));
+    return (P*)d;
+}
 
 template <typename T>
 ALF_D unsigned reserve(unsigned* counter, bool take, unsigned below)
@@ -232,18 +267,24 @@ ALF_D unsigned reserve(unsigned* counter, bool take, unsigned below)
     return base + __popc(bal & below);
 }
 
-// clears the bitmap and seeds the square of half-width r around (ci, cj); returns the dirty-set size
-template <typename T, int NT>
-ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaSweepShared& sh)
+// clears the bitmap and seeds the square of half-width r around (ci, cj); returns the dirty-set size.
+// S: the shared counters (rank 0's with clusters).
+template <typename T, int NT, int CS = 1>
+ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaSweepShared& S)
 {
+    constexpr unsigned STRIDE = (unsigned)(NT * CS);
+    const unsigned tid = cluster_rank<CS>() * NT + threadIdx.x;
     const unsigned below = (1u << (threadIdx.x & 31u)) - 1u;
     const unsigned words = (unsigned)((g.nx * g.ny + 31) / 32);
-    for (unsigned w = threadIdx.x; w < words; w += NT) g.bm[w] = 0u;
-    if (threadIdx.x == 0) sh.cnt[1] = 0u;
-    __syncthreads();
+    for (unsigned w = tid; w < words; w += STRIDE) g.bm[w] = 0u;
+    if (tid == 0) {
+        S.cnt[1] = 0u;
+        S.kmin[0] = ~0ull;
+    }
+    sweep_sync<CS>();
     const int w = 2 * r + 1;
-    for (int base = 0; base < w * w; base += NT) {
-        const int k = base + (int)threadIdx.x;
+    for (int base = 0; base < w * w; base += (int)STRIDE) {
+        const int k = base + (int)tid;
         bool take = false;
         unsigned n = 0u;
         if (k < w * w) {
@@ -253,23 +294,25 @@ ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaS
                 take = !neg_bit(g.tf[n]);
             }
         }
-        const unsigned slot = reserve<T>(&sh.cnt[1], take, below);
+        const unsigned slot = reserve<T>(&S.cnt[1], take, below);
         if (take) {
             g.list0[slot] = n;
             atomicOr(g.bm + (n >> 5), 1u << (n & 31u));
         }
     }
-    __syncthreads();
-    const unsigned nact = sh.cnt[1];
-    __syncthreads();
+    sweep_sync<CS>();
+    const unsigned nact = S.cnt[1];
+    sweep_sync<CS>();
     return nact;
 }
 
-template <typename T, int NT, bool VT = false>
+template <typename T, int NT, bool VT = false, int CS = 1>
 ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds,
-                     CtaSweepShared& sh)
+                     CtaSweepShared& S)
 {
     constexpr int NW = NT / 32;
+    constexpr unsigned STRIDE = (unsigned)(NT * CS);
+    const unsigned tid = cluster_rank<CS>() * NT + threadIdx.x;
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const T inf = alf_inf<T>();
@@ -284,27 +327,37 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
         unsigned* LB = par ? g.list0 : g.list1;
         // front time of the dirty set
         auto m = order_key(inf);
-        for (unsigned k = threadIdx.x; k < nact; k += NT) {
+        for (unsigned k = tid; k < nact; k += STRIDE) {
             const auto v = order_key(tf[LA[k]]);
             m = v < m ? v : m;
         }
         m = warp_min(m);
-        if (lane == 0) sh.kmin[wid] = (unsigned long long)m;
-        if (threadIdx.x == 0) {
-            sh.cnt[0] = 0u;
-            sh.cnt[1] = 0u;
+        if constexpr (CS == 1) {
+            if (lane == 0) S.kmin[wid] = (unsigned long long)m;
+        } else {
+            // one minimum per round in rank 0, double-buffered: this round's slot was reset in the last one
+            if (lane == 0) atomicMin(&S.kmin[par], (unsigned long long)m);
+            if (tid == 0) S.kmin[par ^ 1u] = ~0ull;
         }
-        __syncthreads();
+        if (tid == 0) {
+            S.cnt[0] = 0u;
+            S.cnt[1] = 0u;
+        }
+        sweep_sync<CS>();
         auto mm = order_key(inf);
+        if constexpr (CS == 1) {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const auto v = (decltype(mm))sh.kmin[w];
-            mm = v < mm ? v : mm;
+            for (int w = 0; w < NW; ++w) {
+                const auto v = (decltype(mm))S.kmin[w];
+                mm = v < mm ? v : mm;
+            }
+        } else {
+            mm = (decltype(mm))S.kmin[par];
         }
         const T lim = from_key(mm, T(0)) + g.band;
         // split
-        for (unsigned base = 0; base < nact; base += NT) {
-            const unsigned k = base + threadIdx.x;
+        for (unsigned base = 0; base < nact; base += STRIDE) {
+            const unsigned k = base + tid;
             const bool in = k < nact;
             bool ev = false;
             unsigned n = 0u;
@@ -313,8 +366,8 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                 const T t = tf[n];
                 ev = t <= lim || !(t < inf);
             }
-            const unsigned se = reserve<T>(&sh.cnt[0], in && ev, below);
-            const unsigned sc = reserve<T>(&sh.cnt[1], in && !ev, below);
+            const unsigned se = reserve<T>(&S.cnt[0], in && ev, below);
+            const unsigned sc = reserve<T>(&S.cnt[1], in && !ev, below);
             if (in && ev) {
                 g.el[se] = n;
                 atomicAnd(g.bm + (n >> 5), ~(1u << (n & 31u)));
@@ -322,10 +375,10 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                 LB[sc] = n;
             }
         }
-        __syncthreads();
-        const unsigned ne = sh.cnt[0];
+        sweep_sync<CS>();
+        const unsigned ne = S.cnt[0];
         // evaluate
-        for (unsigned e = threadIdx.x; e < ne; e += NT) {
+        for (unsigned e = tid; e < ne; e += STRIDE) {
             const unsigned n = g.el[e];
             const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
             T nb[12];
@@ -349,10 +402,10 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
             g.nv[e] = v;
         }
         evals += ne;
-        __syncthreads();
+        sweep_sync<CS>();
         // marking
-        for (unsigned base = 0; base < ne; base += NT) {
-            const unsigned e = base + threadIdx.x;
+        for (unsigned base = 0; base < ne; base += STRIDE) {
+            const unsigned e = base + tid;
             bool changed = false, inband = false, act = false;
             unsigned n = 0u;
             int i = 0, j = 0;
@@ -393,13 +446,13 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                         push = (atomicOr(g.bm + (mnode >> 5), bit) & bit) == 0u;
                     }
                 }
-                const unsigned slot = reserve<T>(&sh.cnt[1], push, below);
+                const unsigned slot = reserve<T>(&S.cnt[1], push, below);
                 if (push) LB[slot] = mnode;
             }
         }
-        __syncthreads();
-        nact = sh.cnt[1];
-        __syncthreads();
+        sweep_sync<CS>();
+        nact = S.cnt[1];
+        sweep_sync<CS>();
         par ^= 1u;
     }
     return true;

@@ -155,6 +155,10 @@ def test_host_validation_errors(api):
     with pytest.raises(B.AlfError) as e:
         api.Plan(wl, precision="fp64", sweep=3, cta_threads=96)
     assert e.value.code == 1
+    for bad in ({"cta_cluster": 3}, {"cta_cluster": 2, "cta_threads": 256}):
+        with pytest.raises(B.AlfError) as e:
+            api.Plan(wl, precision="fp64", sweep=3, **bad)
+        assert e.value.code == 1
 
 
 def test_graph_stream_and_timing(api, oracle):
@@ -194,9 +198,33 @@ def test_sweep_schedules_agree(api, oracle):
     assert torch.equal(t1, t2) and torch.equal(t1, t3)
     assert torch.equal(rec1, rec2) and torch.equal(rec1, rec3)
     for nt in (64, 128, 512):  # other numbers of warps on each field's CTA
-        Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_threads=nt)
+        Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_threads=nt, cta_cluster=1)
         assert Pn.options.cta_threads == nt
         assert torch.equal(t1, tn) and torch.equal(rec1, recn)
+    for cs in (2, 4, 8):  # one field shared by a cluster of CTAs on as many SMs
+        Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_cluster=cs)
+        assert Pn.options.cta_cluster == cs and Pn.options.cta_threads == 512
+        assert torch.equal(t1, tn) and torch.equal(rec1, recn)
+
+
+@pytest.mark.parametrize("cs", [2, 4])
+def test_cluster_sweep_fp32(api, oracle, cs):
+    """FP32 fields solved by clusters of CTAs (one field on several SMs) match the FP64 oracle within 1e-4,
+    on a batch of ragged fields; the plan's default for a batch with fewer fields than SMs is a cluster."""
+    wl = W.weld_batch(nsamples=3, nsrc=3, nrec=4, sizes=(96, 160, 224))
+    P, th, times, rt, rec = _solve(api, wl, "fp32", sweep=3, cta_cluster=cs)
+    assert P.options.cta_cluster == cs
+    worst = 0.0
+    for b in range(3):
+        for s in range(3):
+            tau, orec, fr, M = oracle_field(oracle, wl, b, s)
+            worst = max(worst, rel_err(P.field(times, b * 3 + s).cpu().numpy(), tau).max())
+    assert worst < 1e-4
+    Pd = api.Plan(wl, precision="fp32", sweep=3)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert Pd.options.cta_threads == 512 and Pd.options.cta_cluster == max(c for c in (1, 2, 4, 8) if 9 * c <= nsm)
+    td, _ = Pd.solve(th)
+    assert (td - times).abs().max().item() <= 1e-4 * times[torch.isfinite(times)].max().item()
     for b, s in ((0, 0), (3, 2), (5, 3)):
         tau, orec, fr, M = oracle_field(oracle, wl, b, s)
         assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
