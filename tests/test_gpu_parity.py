@@ -205,6 +205,10 @@ def test_sweep_schedules_agree(api, oracle):
         Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_cluster=cs)
         assert Pn.options.cta_cluster == cs and Pn.options.cta_threads == 512
         assert torch.equal(t1, tn) and torch.equal(rec1, recn)
+    for b, s in ((0, 0), (3, 2), (5, 3)):
+        tau, orec, fr, M = oracle_field(oracle, wl, b, s)
+        assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
+        assert record_mismatch(P2.field(rec2, b * 4 + s).cpu().numpy(), orec, fr) == 0
 
 
 @pytest.mark.parametrize("cs", [2, 4])
@@ -225,7 +229,3 @@ def test_cluster_sweep_fp32(api, oracle, cs):
     assert Pd.options.cta_threads == 512 and Pd.options.cta_cluster == max(c for c in (1, 2, 4, 8) if 9 * c <= nsm)
     td, _ = Pd.solve(th)
     assert (td - times).abs().max().item() <= 1e-4 * times[torch.isfinite(times)].max().item()
-    for b, s in ((0, 0), (3, 2), (5, 3)):
-        tau, orec, fr, M = oracle_field(oracle, wl, b, s)
-        assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
-        assert record_mismatch(P2.field(rec2, b * 4 + s).cpu().numpy(), orec, fr) == 0
