@@ -46,7 +46,8 @@ OPS_PER_EVAL = 627.0
 # DRAM bytes (read + write) per evaluation of each sweep kernel, from one ncu capture of a 2,560-field
 # solve (80 weld samples x 32 sources); scaled to a launch by its evaluations.  None for a kernel that
 # changed since its capture.
-TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel": None}
+TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel<64>": None, "fim_cta_kernel<128>": None,
+                          "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
 SMS, FP32_LANES = 152, 128
 
 
@@ -65,6 +66,8 @@ def _args():
                     help="profiling run: the whole step, or the travel-time solve alone")
     ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2, 3],
                     help="profiling run: sweep schedule (0: the library's choice)")
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
+                    help="profiling run: threads of a field's CTA in sweep 3 (0: the library's choice)")
     return ap.parse_args()
 
 
@@ -192,7 +195,7 @@ def profile_run(args, wl, api, local):
     import torch
     full = args.profile_stages == "all"
     P = api.Plan(wl, precision="fp32", device=local, keep_records=int(full), use_graph=0, band_cells=2.0,
-                 sweep=args.sweep)
+                 sweep=args.sweep, cta_threads=args.cta_threads)
     th = P.theta_tensor()
     times, rect = P.new_times(), P.new_rec_times()
     rec = P.new_records() if full else None
@@ -314,7 +317,7 @@ def main():
     # ---- roofline of the dominant kernel (the evaluation of the local operator): its launches timed with
     # CUDA events on the solve's stream, over a second run of the same solves
     Pt = api.Plan(wl, precision="fp32", device=local, time_kernels=1, band_cells=P.options.band_cells,
-                  sweep=P.options.sweep)
+                  sweep=P.options.sweep, cta_threads=P.options.cta_threads, cta_cluster=P.options.cta_cluster)
     tt = Pt.new_times()
     Pt.solve(th, times=tt)
     ev_ms, evals, eval_launches = 0.0, 0, 0
@@ -330,6 +333,8 @@ def main():
     peak = SMS * FP32_LANES * clock * 1e6 / 1e12
     evals_per_node = evals / (args.steps * P.total_nodes)
     kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel"}[P.options.sweep]
+    if P.options.sweep == 3:  # the CTA shape decides how many fields share the L2, hence the traffic
+        kname += f"<{P.options.cta_threads}>" + (f"x{P.options.cta_cluster}" if P.options.cta_cluster > 1 else "")
     del Pt, tt
 
     # ---- end to end through the public API: orientations from pinned host memory, receiver times back

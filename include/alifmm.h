@@ -131,7 +131,8 @@ typedef struct {
                                SMs, else 256.  alf_plan_autotune chooses it among the four. */
     int cta_cluster;        /* sweep 3: CTAs of 512 threads that share one field as a thread-block cluster on
                                as many SMs, 1, 2, 4 or 8; 0 = choose (default): for FP32 batches with no more
-                               fields than SMs, the largest that keeps fields x cluster <= SMs, else 1 */
+                               fields than SMs, the largest that keeps fields x cluster <= SMs and leaves at
+                               least 2^19 nodes of the largest field per SM, else 1 */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */

@@ -33,8 +33,11 @@ def test_large_medium_full_size(api, oracle):
     times, rt = P.solve(th, records=rec)
     assert P.status() == 0
     st = P.stats()
-    print(f"2048^2 x 64: sweep {P.options.sweep}, evaluations/node {st['evaluations'] / st['nodes']:.2f}, "
-          f"rounds {st['rounds']}")
+    print(f"2048^2 x 64: sweep {P.options.sweep}, {P.options.cta_threads} threads x {P.options.cta_cluster} CTAs "
+          f"per field, evaluations/node {st['evaluations'] / st['nodes']:.2f}, rounds {st['rounds']}")
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    if nsm >= 128:  # 64 fields of 2^22 nodes: a cluster of 2 SMs on each
+        assert P.options.sweep == 3 and P.options.cta_cluster == 2
     mr, fl = P.check64(th, times, rec)
     torch.cuda.synchronize()
     print(f"FP64 check: max residual {mr.max().item():.3e}, record flips {int(fl.sum())} of {P.total_nodes}")
