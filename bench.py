@@ -46,8 +46,8 @@ OPS_PER_EVAL = 627.0
 # DRAM bytes (read + write) per evaluation of each sweep kernel, from one ncu capture of a 2,560-field
 # solve (80 weld samples x 32 sources); scaled to a launch by its evaluations.  None for a kernel that
 # changed since its capture.
-TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel<64>": None, "fim_cta_kernel<128>": None,
-                          "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
+TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel<64>": 6.00, "fim_cta_kernel<128>": 3.41,
+                          "fim_cta_kernel<256>": 2.96, "fim_cta_kernel<512>": 2.72}
 SMS, FP32_LANES = 152, 128
 
 
@@ -418,6 +418,7 @@ def main():
                                 "nodes_per_s": PL.total_nodes / (e0.elapsed_time(e1) * 1e-3),
                                 "rays_per_s": PL.nfields * PL.nrec / (e1.elapsed_time(e2) * 1e-3),
                                 "sweep": PL.options.sweep, "cta_threads": PL.options.cta_threads,
+                                "cta_cluster": PL.options.cta_cluster,
                                 "status": PL.status()}
         del PL, tL
         # gradient: 256 samples x 32 sources on 200 x 200, forward (records) + adjoint
