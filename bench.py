@@ -429,6 +429,7 @@ def main():
         _, tob = Pt3.solve(Pt3.theta_tensor())
         tob = (tob + torch.as_tensor(W.observation_noise(tuple(tob.shape)), device=tob.device).float())
         t3, r3, c3 = P3.new_times(), P3.new_rec_times(), P3.new_records()
+        P3.autotune(th3, t3, c3)
 
         def grad_step():
             P3.solve(th3, times=t3, rec_times=r3, records=c3)
@@ -442,6 +443,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         line["grad_ms"] = e0.elapsed_time(e1) / 3
+        line["grad_schedule"] = {"sweep": P3.options.sweep, "band_cells": P3.options.band_cells,
+                                 "cta_threads": P3.options.cta_threads}
         line["grad_config"] = "256 samples x 32 sources x 32 receivers, 200 x 200, FP32 forward + adjoint"
         del P3, Pt3
     if rank == 0:
