@@ -188,12 +188,16 @@ alf_status alf_plan_options(const alf_plan* plan, alf_options* out);
 
 /* Forward solve (Secs. 2, 4): for every field, the near-source initialisation
  * then the ALI local update iterated to its fixed point (the heap FMM's
- * result) by bulk-synchronous sweep rounds over all fields of the plan: each
- * round re-evaluates, in every field, the dirty nodes (those whose
- * neighbourhood changed) near the front, until every dirty set is empty.
- * The call enqueues the rounds on `stream` and synchronises it every 32
- * rounds to read the remaining work, so it returns once the sweep is done
- * (the finalisation and receiver gather are still enqueued, not waited for).
+ * result) by sweep rounds: each round re-evaluates, in a field, the dirty
+ * nodes (those whose neighbourhood changed) near the front, until every dirty
+ * set is empty.  Sweeps 2 and 3 run every field's rounds inside one launch
+ * (one warp, one CTA or one cluster of CTAs per field, fields taken from a
+ * queue), so the call only enqueues work on `stream` (it waits only when the
+ * plan times its kernels).  Sweep 1 enqueues lockstep rounds over all fields
+ * and synchronises `stream` every 32 rounds to read the remaining work, so it
+ * returns once the rounds are done (the finalisation and receiver gather are
+ * still enqueued, not waited for).  Every schedule reaches the same fixed
+ * point, bit for bit.
  *  region_theta   [nsamples][nregions] double, orientation of each region
  *  times          [total nodes] float (ALF_FP32) or double (ALF_FP64), output
  *  rec_times      [nsamples][nsources][nreceivers], same dtype, output; may be NULL
@@ -277,10 +281,12 @@ typedef struct {
 alf_status alf_plan_stats(alf_plan* plan, void* stream, alf_stats* out);
 
 /* Picks the sweep's launch parameters for this plan by timing full solves
- * of its batch and keeps the fastest: the schedule (unless the options fix
- * it), the front band width (1..6 cells) and, for sweep 1, the evaluation
- * CTA size (128 or 256 threads).  `times` and `records` (may be NULL) are
- * scratch outputs of those solves.  Synchronous. */
+ * of its batch (the faster of two per candidate) and keeps the fastest: the
+ * schedule (unless the options fix it), the front band width (1..6 cells)
+ * and, for sweep 1, the evaluation CTA size (128 or 256 threads), for sweep 3
+ * the threads per field's CTA (64..512, unless fixed) and, where the fields
+ * leave SMs idle, a cluster of 2, 4 or 8 CTAs per field.  `times` and
+ * `records` (may be NULL) are scratch outputs of those solves.  Synchronous. */
 alf_status alf_plan_autotune(alf_plan* plan, const double* region_theta, void* times, uint8_t* records,
                              void* stream);
 
