@@ -68,6 +68,9 @@ def _args():
                     help="profiling run: sweep schedule (0: the library's choice)")
     ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
                     help="profiling run: threads of a field's CTA in sweep 3 (0: the library's choice)")
+    ap.add_argument("--profile-workload", default="batch", choices=["batch", "plain"],
+                    help="profiling run: the weld batch (--samples x 32 sources) or the plain single medium "
+                         "(256 x 256 weld, 32 sources)")
     return ap.parse_args()
 
 
@@ -210,7 +213,8 @@ def profile_run(args, wl, api, local):
     st = P.stats()
     print(json.dumps({"profile_run": True, "fields": P.nfields, "nodes": P.total_nodes, "status": P.status(),
                       "evaluations_last_solve": st["evaluations"], "rounds_last_solve": st["rounds"],
-                      "sweep": P.options.sweep, "stages": args.profile_stages,
+                      "sweep": P.options.sweep, "cta_threads": P.options.cta_threads,
+                      "cta_cluster": P.options.cta_cluster, "stages": args.profile_stages,
                       "seconds": time.perf_counter() - t0}), flush=True)
 
 
@@ -237,7 +241,7 @@ def main():
 
     wl = rank_workload(W, args.samples, rank)
     if args.profile:
-        return profile_run(args, wl, api, local)
+        return profile_run(args, W.weld_single() if args.profile_workload == "plain" else wl, api, local)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     P = api.Plan(wl, precision="fp32", device=local, keep_records=1)
