@@ -282,7 +282,8 @@ alf_status alf_plan_stats(alf_plan* plan, void* stream, alf_stats* out);
 
 /* Picks the sweep's launch parameters for this plan by timing full solves
  * of its batch (the faster of two per candidate) and keeps the fastest: the
- * schedule (unless the options fix it), the front band width (1..6 cells)
+ * schedule (unless the options fix it), the front band width (1..6 cells,
+ * in half cells between 1 and 2.5)
  * and, for sweep 1, the evaluation CTA size (128 or 256 threads), for sweep 3
  * the threads per field's CTA (64..512, unless fixed) and, where the fields
  * leave SMs idle, a cluster of 2, 4 or 8 CTAs per field.  `times` and

@@ -952,10 +952,11 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     if (try1)
         for (double band : {2.0, 3.0, 4.0, 6.0})
             for (int blk : {128, 256}) cands.push_back({1, band, blk, 1});
+    // bands of the field-resident schedules: measured optima lie between 1.5 and 2.5 cells on weld media
     if (try2)
-        for (double band : {1.0, 2.0, 3.0, 4.0, 6.0}) cands.push_back({2, band, p->eval_block, 1});
+        for (double band : {1.0, 1.5, 2.0, 2.5, 3.0, 4.0}) cands.push_back({2, band, p->eval_block, 1});
     if (p->opt.sweep == 0 || p->opt.sweep == 3)
-        for (double band : {1.0, 2.0, 3.0, 4.0}) {
+        for (double band : {1.0, 1.5, 2.0, 2.5, 3.0}) {
             if (p->opt.cta_cluster <= 1)
                 for (int nt : {64, 128, 256, 512})
                     if (p->opt.cta_threads == 0 || p->opt.cta_threads == nt) cands.push_back({3, band, nt, 1});

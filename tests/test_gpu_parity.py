@@ -182,7 +182,7 @@ def test_graph_stream_and_timing(api, oracle):
     assert st["eval_launches"] > 0 and st["eval_ms"] > 0 and st["kernel_launches"] > 0
     assert (t3 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
     opt = Pt.autotune(th)
-    assert opt.band_cells in (1.0, 2.0, 3.0, 4.0, 6.0) and opt.sweep in (1, 2, 3)
+    assert opt.band_cells in (1.0, 1.5, 2.0, 2.5, 3.0, 4.0, 6.0) and opt.sweep in (1, 2, 3)
     assert opt.cta_threads in (64, 128, 256, 512)
     t4, _ = Pt.solve(th)
     assert (t4 - ref).abs().max().item() <= 1e-4 * ref[torch.isfinite(ref)].max().item()
