@@ -89,3 +89,22 @@ def test_velocity_table_backward_is_refused(api):
     with pytest.raises(B.AlfError) as e:
         P.backward(th, times, rec, rt)
     assert e.value.code == 8
+
+
+def test_velocity_table_schedules_agree(api):
+    """The velocity-table kernels of every schedule (lockstep rounds, warp per field, CTA per field of each
+    size, clusters) reach the same fixed point: FP64 fields and records identical bit for bit."""
+    wl = W.weld_batch(nsamples=3, nsrc=2, nrec=3, sizes=(48, 96))
+    ref = None
+    for opts in ({"sweep": 1}, {"sweep": 2}, {"sweep": 3, "cta_threads": 64, "cta_cluster": 1},
+                 {"sweep": 3, "cta_threads": 256, "cta_cluster": 1}, {"sweep": 3, "cta_cluster": 2}):
+        P = api.Plan(wl, precision="fp64", velocity_table=1, **opts)
+        th = P.theta_tensor()
+        rec = P.new_records()
+        times, _ = P.solve(th, records=rec)
+        assert P.status() == 0
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = (times, rec)
+        else:
+            assert torch.equal(ref[0], times) and torch.equal(ref[1], rec), opts
