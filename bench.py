@@ -46,7 +46,7 @@ OPS_PER_EVAL = 627.0
 # DRAM bytes (read + write) per evaluation of each sweep kernel, from one ncu capture of a 2,560-field
 # solve (80 weld samples x 32 sources); scaled to a launch by its evaluations.  None for a kernel that
 # changed since its capture.
-TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": 16.93, "fim_cta_kernel<64>": 5.90, "fim_cta_kernel<128>": 3.31,
+TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": None, "fim_cta_kernel<64>": 5.90, "fim_cta_kernel<128>": 3.31,
                           "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
 SMS, FP32_LANES = 152, 128
 

@@ -151,53 +151,64 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
         evals += ne;
         __syncwarp();
         // marking: changed nodes wake their later known neighbours; in-band nodes seed
-        // their unknown neighbours; an out-of-band node with unknown neighbours waits
+        // their unknown neighbours; an out-of-band node with unknown neighbours waits.  A lane's
+        // push decisions come first (plain loads), then its dirty-bit test-and-sets (issued
+        // independently of one another), then its slots (a warp prefix sum of the counts).
         for (unsigned base = 0; base < ne; base += 32u) {
             const unsigned e = base + lane;
-            bool changed = false, inband = false, act = false;
+            unsigned pm = 0u;  // bit q < 12: neighbour q; bit 12: the node itself (seeds later)
             unsigned n = 0u;
             int i = 0, j = 0;
-            T v = inf, lo = inf;
             if (e < ne) {
                 const T o = g.ov[e];
-                v = g.nv[e];
-                changed = !same_bits(o, v);
-                inband = v <= lim;
-                act = changed || inband;
+                const T v = g.nv[e];
+                const bool changed = !same_bits(o, v);
+                const bool inband = v <= lim;
                 n = g.el[e];
                 i = (int)(n % (unsigned)nx);
                 j = (int)(n / (unsigned)nx);
-                lo = v < o ? v : o;
-            }
-            bool seeds_later = false;
+                if (changed || inband) {
+                    const T lo = v < o ? v : o;
+                    bool seeds_later = false;
 #pragma unroll
-            for (int q = 0; q < 13; ++q) {
-                bool push = false;
-                unsigned mnode = n;
-                if (act) {
-                    if (q < 12) {
+                    for (int q = 0; q < 12; ++q) {
                         const int ii = i + sdi(q), jj = j + sdj(q);
                         if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
-                            mnode = (unsigned)(jj * nx + ii);
-                            const T tm = tf[mnode];
+                            const T tm = tf[jj * nx + ii];
                             if (!neg_bit(tm)) {
+                                bool push = false;
                                 if (tm < inf) push = changed && lo <= tm;
                                 else if (inband) push = true;
                                 else seeds_later = true;
+                                pm |= push ? 1u << q : 0u;
                             }
                         }
-                    } else {
-                        push = seeds_later && v < inf;
                     }
-                    if (push) {
-                        const unsigned bit = 1u << (mnode & 31u);
-                        push = (atomicOr(g.bm + (mnode >> 5), bit) & bit) == 0u;
-                    }
+                    if (seeds_later && v < inf) pm |= 1u << 12;
                 }
-                const unsigned bp = __ballot_sync(FULL, push);
-                if (push) LB[nc + __popc(bp & below)] = mnode;
-                nc += __popc(bp);
+                unsigned dup = 0u;
+#pragma unroll
+                for (int q = 0; q < 13; ++q)
+                    if ((pm >> q) & 1u) {
+                        const unsigned mnode = q < 12 ? (unsigned)((j + sdj(q)) * nx + (i + sdi(q))) : n;
+                        const unsigned bit = 1u << (mnode & 31u);
+                        dup |= (atomicOr(g.bm + (mnode >> 5), bit) & bit) ? 1u << q : 0u;
+                    }
+                pm &= ~dup;
             }
+            const unsigned cnt = (unsigned)__popc(pm);
+            unsigned incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if ((int)lane >= o) incl += y;
+            }
+            unsigned slot = nc + incl - cnt;
+#pragma unroll
+            for (int q = 0; q < 13; ++q)
+                if ((pm >> q) & 1u)
+                    LB[slot++] = q < 12 ? (unsigned)((j + sdj(q)) * nx + (i + sdi(q))) : n;
+            nc += __shfl_sync(FULL, incl, 31);
         }
         __syncwarp();
         nact = nc;
