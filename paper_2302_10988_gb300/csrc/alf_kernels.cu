@@ -558,16 +558,16 @@ static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
                                 (int)*smem);
 }
 
-template <typename T, int NT, bool VT, int CS>
-static cudaLaunchConfig_t cta_config(int grid, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr)
+// launch configuration of a cluster launch: nt threads per CTA, clusters of cs CTAs along x
+static cudaLaunchConfig_t cta_config(int grid, int nt, int cs, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(NT);
+    cfg.blockDim = dim3((unsigned)nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.x = (unsigned)cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -587,7 +587,7 @@ static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned
         e = cudaGetLastError();
     } else {
         cudaLaunchAttribute attr[1];
-        const cudaLaunchConfig_t cfg = cta_config<T, NT, VT, CS>(grid, smem, st, attr);
+        const cudaLaunchConfig_t cfg = cta_config(grid, NT, CS, smem, st, attr);
         e = cudaLaunchKernelEx(&cfg, fim_cta_kernel<T, NT, VT, CS>, a, order, smem_words);
     }
     note_launches(1);
@@ -639,7 +639,7 @@ static int fim_cta_occ(unsigned smem_words, int nsm)
         return n * nsm;
     } else {
         cudaLaunchAttribute attr[1];
-        const cudaLaunchConfig_t cfg = cta_config<T, NT, VT, CS>(CS * nsm, smem, nullptr, attr);
+        const cudaLaunchConfig_t cfg = cta_config(CS * nsm, NT, CS, smem, nullptr, attr);
         if (cudaOccupancyMaxActiveClusters(&n, fim_cta_kernel<T, NT, VT, CS>, &cfg) != cudaSuccess) return 0;
         return n * CS;
     }
