@@ -627,6 +627,59 @@ double om_F_node(const om_medium* M, const uint8_t* frozen, const double* tau, i
     return u;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The update of a solved field with the known set fixed by the node's own   */
+/* time: S_D = frozen neighbours + the non-frozen finite neighbours whose key */
+/* (tau, index) precedes (tau_D, idx_D), and the check value U(S_D) (the     */
+/* FP64 convergence check of a field solved in lower precision).  At the     */
+/* causal fixed point the walk of om_F_node stops exactly at this set (every  */
+/* neighbour it accepted precedes D, [R17], and the next one does not), so    */
+/* U(S_D) = tau_D there, with the same record.  Frozen nodes and nodes        */
+/* without a value return their time with record -2 / -1.                     */
+/* Parity: pinned by that fixed-point identity on solved weld fields.         */
+/* ------------------------------------------------------------------------ */
+double om_F_check_node(const om_medium* M, const uint8_t* frozen, const double* tau, int i, int j, int* rec_out)
+{
+    int nx = M->nx;
+    int d = j * nx + i;
+    if (frozen[d]) {
+        *rec_out = -2;
+        return tau[d];
+    }
+    if (!(tau[d] < OM_INF)) {
+        *rec_out = -1;
+        return tau[d];
+    }
+    int known[12], nknown = 0;
+    double t[12];
+    for (int k = 0; k < 12; ++k) {
+        int ii = i + DIAMOND[k][0], jj = j + DIAMOND[k][1];
+        known[k] = 0;
+        t[k] = OM_INF;
+        if (!in_grid(M, ii, jj)) continue;
+        int n = jj * nx + ii;
+        t[k] = tau[n];
+        if (frozen[n] || t[k] < tau[d] || (t[k] == tau[d] && n < d)) {
+            known[k] = 1;
+            ++nknown;
+        }
+    }
+    int urec = -1;
+    double u = nknown ? update_from_set(M, i, j, known, t, &urec) : OM_INF;
+    *rec_out = urec;
+    return u;
+}
+
+void om_F_check_all(const om_medium* M, const uint8_t* frozen, const double* tau_in, double* tau_out, int16_t* rec)
+{
+    for (int j = 0; j < M->ny; ++j)
+        for (int i = 0; i < M->nx; ++i) {
+            int r;
+            tau_out[j * M->nx + i] = om_F_check_node(M, frozen, tau_in, i, j, &r);
+            if (rec) rec[j * M->nx + i] = (int16_t)r;
+        }
+}
+
 /* One simultaneous (Jacobi) application of F to every node. */
 void om_F_all(const om_medium* M, const uint8_t* frozen, const double* tau_in, double* tau_out, int16_t* rec)
 {

@@ -82,6 +82,8 @@ def lib():
             L.om_F_node.argtypes = [P(Medium), P(C.c_uint8), P(C.c_double), C.c_int, C.c_int, P(C.c_int)]
             L.om_F_all.restype = None
             L.om_F_all.argtypes = [P(Medium), P(C.c_uint8), P(C.c_double), P(C.c_double), P(C.c_int16)]
+            L.om_F_check_all.restype = None
+            L.om_F_check_all.argtypes = [P(Medium), P(C.c_uint8), P(C.c_double), P(C.c_double), P(C.c_int16)]
             L.om_jacobi.restype = C.c_int
             L.om_jacobi.argtypes = [P(Medium), P(C.c_uint8), P(C.c_double), P(C.c_int16), C.c_int]
             L.om_init_radius.restype = None
@@ -209,6 +211,19 @@ def F_all(M: OMedium, frozen, tau):
     rec = np.empty(tin.size, np.int16)
     lib().om_F_all(C.byref(M.c), _ptr(frozen, C.c_uint8), _ptr(tin, C.c_double), _ptr(tout, C.c_double),
                    _ptr(rec, C.c_int16))
+    return tout.reshape(M.ny, M.nx), rec.reshape(M.ny, M.nx)
+
+
+def F_check(M: OMedium, frozen, tau):
+    """The update of every node of a solved field with its known set fixed by its own time (frozen neighbours
+    and those whose key (tau, index) precedes the node's): the FP64 convergence check of a field solved in
+    lower precision.  Equals tau, with the solve's records, at the causal fixed point."""
+    frozen = np.ascontiguousarray(frozen, np.uint8).reshape(-1)
+    tin = np.ascontiguousarray(tau, np.float64).reshape(-1)
+    tout = np.empty_like(tin)
+    rec = np.empty(tin.size, np.int16)
+    lib().om_F_check_all(C.byref(M.c), _ptr(frozen, C.c_uint8), _ptr(tin, C.c_double), _ptr(tout, C.c_double),
+                         _ptr(rec, C.c_int16))
     return tout.reshape(M.ny, M.nx), rec.reshape(M.ny, M.nx)
 
 

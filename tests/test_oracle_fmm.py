@@ -36,6 +36,9 @@ def test_heap_equals_fixed_point_and_jacobi_tiny(oracle):
         assert np.array_equal(tau, tj) and np.array_equal(rec, rj)
         F, rF = oracle.F_all(M, frozen, tau)
         assert np.array_equal(F, tau) and np.array_equal(rF, rec)
+        # the check's evaluation (known set fixed by each node's own key) is the identity there too
+        Fc, rc = oracle.F_check(M, frozen, tau)
+        assert np.array_equal(Fc, tau) and np.array_equal(rc, rec)
 
 
 def test_heap_is_causal_on_weld(oracle):
@@ -51,6 +54,8 @@ def test_heap_is_causal_on_weld(oracle):
         assert all(keys[a] < keys[a + 1] for a in range(len(keys) - 1))
         F, _ = oracle.F_all(M, fr, tau)
         assert np.array_equal(F, tau)
+        Fc, rc = oracle.F_check(M, fr, tau)
+        assert np.array_equal(Fc, tau) and np.array_equal(rc, rec)
 
 
 @pytest.mark.parametrize("ang_deg,th_deg", [(80.0, 30.0), (60.0, -20.0), (100.0, 65.0), (90.0, 0.0)])
@@ -222,3 +227,26 @@ def test_velocity_table_exact_at_integer_degrees(oracle):
     a = oracle.stencil_value(M0, tau.reshape(-1), 4, 4, 1)
     b = oracle.stencil_value(M1, tau.reshape(-1), 4, 4, 1)
     assert a != b and abs(b / a - 1) < 1e-4
+
+
+def test_check_evaluation_with_exact_ties(oracle):
+    """On a homogeneous isotropic grid with a central source, mirror-image nodes get bit-identical times, and
+    many of them are diamond neighbours of one another: the key order (tau, index) decides which of two tied
+    nodes is known to the other.  The check's evaluation with its known set fixed by each node's own key
+    reproduces the field, records included, exactly at those ties."""
+    n = 21
+    m = oracle.mat_from_voigt(*W.PARENT_ISO)
+    M = oracle.OMedium(n, n, 1e-3, np.zeros(n * n, np.int64), np.zeros(n * n), [m])
+    fr, t0 = oracle.init_radius(M, n // 2, n // 2, 0)
+    tau, rec, st = oracle.fmm(M, fr, t0)
+    assert st["unreached"] == 0
+    ties = 0
+    for j in range(n):
+        for i in range(n):
+            for di, dj in ((1, 1), (1, -1), (2, 0), (0, 2), (1, 0), (0, 1)):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < n and 0 <= jj < n and tau[j, i] == tau[jj, ii]:
+                    ties += 1
+    assert ties > 20  # the field does exercise the tie order
+    Fc, rc = oracle.F_check(M, fr, tau)
+    assert np.array_equal(Fc, tau) and np.array_equal(rc, rec)
