@@ -970,12 +970,20 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     const int eval_block0 = p->eval_block;
     int best_block = p->sweep_mode == 3 ? p->cta_threads : p->eval_block, best_mode = p->sweep_mode;
     int best_cluster = p->cta_cluster;
+    // the plan's settings before tuning, put back if a candidate fails
+    const double band0 = p->opt.band_cells;
+    const int mode0 = p->sweep_mode, threads0 = p->cta_threads, cluster0 = p->cta_cluster;
     cudaEvent_t e0, e1;
     ALF_CUDA(ctx, cudaEventCreate(&e0));
-    ALF_CUDA(ctx, cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, ALF_ERR_CUDA, "alf_plan_autotune: cudaEventCreate failed");
+    }
     const int keep_timing = p->opt.time_kernels;
     p->opt.time_kernels = 0;
-    for (const Cand& c : cands) {
+    // one candidate: a warm-up solve (graph capture), then the faster of two timed solves (the candidates
+    // often differ by a few %)
+    auto time_candidate = [&](const Cand& c, float* ms) -> alf_status {
         p->opt.band_cells = c.band;
         p->eval_block = c.mode == 1 ? c.block : eval_block0;
         if (c.mode == 3) set_cta_shape(p, c.block, c.cluster, p->opt.precision, p->opt.velocity_table != 0);
@@ -984,10 +992,10 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
             cudaGraphExecDestroy(p->chunk_graph);
             p->chunk_graph = nullptr;
         }
-        alf_status rc = alf_solve(p, theta, times, nullptr, records, stream);  // warm-up (graph capture)
+        alf_status rc = alf_solve(p, theta, times, nullptr, records, stream);
         if (rc != ALF_OK) return rc;
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {  // the faster of two solves: the candidates often differ by a few %
+        *ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
             ALF_CUDA(ctx, cudaEventRecord(e0, st));
             rc = alf_solve(p, theta, times, nullptr, records, stream);
             if (rc != ALF_OK) return rc;
@@ -995,8 +1003,15 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
             ALF_CUDA(ctx, cudaEventSynchronize(e1));
             float m = 0.f;
             ALF_CUDA(ctx, cudaEventElapsedTime(&m, e0, e1));
-            ms = std::min(ms, m);
+            *ms = std::min(*ms, m);
         }
+        return ALF_OK;
+    };
+    alf_status status = ALF_OK;
+    for (const Cand& c : cands) {
+        float ms = 0.f;
+        status = time_candidate(c, &ms);
+        if (status != ALF_OK) break;
         if (ms < best_ms) {
             best_ms = ms;
             best_band = c.band;
@@ -1007,6 +1022,18 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    p->opt.time_kernels = keep_timing;
+    if (p->chunk_graph) {
+        cudaGraphExecDestroy(p->chunk_graph);
+        p->chunk_graph = nullptr;
+    }
+    if (status != ALF_OK) {
+        p->opt.band_cells = band0;
+        p->eval_block = eval_block0;
+        set_cta_shape(p, threads0, cluster0, p->opt.precision, p->opt.velocity_table != 0);
+        p->sweep_mode = mode0;
+        return status;
+    }
     p->opt.band_cells = best_band;
     p->eval_block = best_mode == 1 ? best_block : eval_block0;
     if (best_mode == 3)
@@ -1016,11 +1043,6 @@ alf_status alf_plan_autotune(alf_plan* p, const double* theta, void* times, uint
                       p->opt.cta_cluster ? p->opt.cta_cluster : p->cluster_default, p->opt.precision,
                       p->opt.velocity_table != 0);
     p->sweep_mode = best_mode;
-    p->opt.time_kernels = keep_timing;
-    if (p->chunk_graph) {
-        cudaGraphExecDestroy(p->chunk_graph);
-        p->chunk_graph = nullptr;
-    }
     return ALF_OK;
 }
 
