@@ -33,9 +33,9 @@
  *  - Every call returns an alf_status.  Arguments are validated on the host
  *    before anything is launched; on failure nothing is enqueued and
  *    alf_last_error() describes the problem.  Kernels never trap: device-side
- *    failures (no convergence, a queue wait that ran out, an incomplete ray)
- *    are written to the plan's status words and read back by
- *    alf_sync_status().
+ *    failures (no convergence, an incomplete ray, an adjoint sweep that could
+ *    not release every node) are written to the plan's status words and read
+ *    back by alf_sync_status().
  */
 #ifndef ALIFMM_H
 #define ALIFMM_H
@@ -50,14 +50,16 @@ extern "C" {
 typedef enum {
     ALF_OK = 0,
     ALF_ERR_INVALID_ARG = 1,          /* a pointer, size or option is out of range */
-    ALF_ERR_NONPHYSICAL_MATERIAL = 2, /* rho <= 0, non-finite stiffness, or qP lambda <= 0 */
+    ALF_ERR_NONPHYSICAL_MATERIAL = 2, /* rho <= 0, non-finite stiffness, or an in-plane stiffness that is not
+                                         positive definite (c22, c33, c44 > 0 and c22 c33 > c23^2) */
     ALF_ERR_OUT_OF_GRID = 3,          /* a source or receiver node lies outside its grid */
     ALF_ERR_CUDA = 4,                 /* a CUDA runtime call failed (message has the CUDA error) */
     ALF_ERR_OOM = 5,                  /* a workspace allocation failed */
     ALF_ERR_NOT_CONVERGED = 6,        /* the sweeps hit their visit cap before reaching the fixed point */
     ALF_ERR_RAY_INCOMPLETE = 7,       /* a ray hit its point cap before reaching its target */
     ALF_ERR_UNSUPPORTED = 8,          /* a feature not available in this build */
-    ALF_ERR_QUEUE_TIMEOUT = 9         /* a device-side work-queue wait ran out (bounded spin) */
+    ALF_ERR_INCONSISTENT_RECORDS = 9  /* alf_backward: some node was never released by the reverse sweep
+                                         (the records or times do not come from one solve of this plan) */
 } alf_status;
 
 typedef enum { ALF_FP64 = 0, ALF_FP32 = 1 } alf_precision;
@@ -302,18 +304,23 @@ alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, in
  * no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- an application whose device memory belongs to another
  * allocator, or a latency-bound loop in which cudaMalloc/cudaFree, which can
- * synchronise the device, are not allowed).  It runs the same kernels as
- * alf_solve in FP32 with the radius initialisation, but keeps every workspace
- * in a fixed device array inside the library (about 7 MB per GPU that loads
- * the library, held until the process exits).
+ * synchronise the device, are not allowed).  It runs the lockstep-round
+ * kernels of alf_solve (sweep 1) in FP32 with the radius initialisation and
+ * the plan's default front band (2 cell-crossing times), but keeps every
+ * workspace in a fixed device array inside the library (about 7 MB per GPU
+ * that loads the library, held until the process exits).
  * Limits: nx*ny <= 512*512 nodes, nregions <= 1024, nmaterials <= 64,
  * init_radius <= 8; larger inputs are rejected with ALF_ERR_INVALID_ARG and a
  * message in err.
  *  cuda_device              device to run on (made current)
  *  materials[nmaterials]    host
- *  region_material[nregions], region_theta[nregions] (double), region_map[ny][nx]   device, input
+ *  region_material[nregions], region_theta[nregions] (double), region_map[ny][nx]   device, input;
+ *                           every region id must be < nregions and every material id < nmaterials (checked
+ *                           on the device before any other kernel runs: ALF_ERR_INVALID_ARG otherwise)
  *  h, (si, sj)              spacing (m) and source node
  *  group_model              alf_group_model
+ *  max_rounds               cap on the sweep rounds (0: 64 (nx + ny)); a field still changing after it
+ *                           returns ALF_ERR_NOT_CONVERGED
  *  times[ny][nx]            device float, output (caller-owned)
  *  stream                   cudaStream_t as void*; the call synchronises it
  *  err, err_len             host buffer for a message (may be NULL)
@@ -326,8 +333,8 @@ alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, in
 alf_status alf_solve_field_noalloc(int cuda_device, const alf_material* materials, int nmaterials,
                                    const uint16_t* region_material, int nregions, const double* region_theta,
                                    const uint16_t* region_map, int nx, int ny, double h, int si, int sj,
-                                   int init_radius, int group_model, float* times, void* stream, char* err,
-                                   size_t err_len);
+                                   int init_radius, int group_model, int max_rounds, float* times, void* stream,
+                                   char* err, size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libalifmm.so")
 ALF_OK = 0
 STATUS_NAMES = {0: "ALF_OK", 1: "ALF_ERR_INVALID_ARG", 2: "ALF_ERR_NONPHYSICAL_MATERIAL", 3: "ALF_ERR_OUT_OF_GRID",
                 4: "ALF_ERR_CUDA", 5: "ALF_ERR_OOM", 6: "ALF_ERR_NOT_CONVERGED", 7: "ALF_ERR_RAY_INCOMPLETE",
-                8: "ALF_ERR_UNSUPPORTED", 9: "ALF_ERR_QUEUE_TIMEOUT"}
+                8: "ALF_ERR_UNSUPPORTED", 9: "ALF_ERR_INCONSISTENT_RECORDS"}
 ALF_FP64, ALF_FP32 = 0, 1
 ALF_GROUP_PAPER, ALF_GROUP_EXACT = 0, 1
 ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
@@ -113,8 +113,8 @@ def load(path: str = LIB_PATH):
         L.alf_plan_autotune.argtypes = [vp, vp, vp, vp, vp]
         L.alf_solve_field_noalloc.restype = C.c_int
         L.alf_solve_field_noalloc.argtypes = [C.c_int, P(alf_material), C.c_int, vp, C.c_int, vp, vp, C.c_int,
-                                              C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
-                                              C.c_char_p, C.c_size_t]
+                                              C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp,
+                                              vp, C.c_char_p, C.c_size_t]
         L.alf_eval_velocity.restype = C.c_int
         L.alf_eval_velocity.argtypes = [vp, P(alf_material), C.c_int, C.c_int, C.c_int, vp, vp, C.c_int, vp]
         _lib = L
@@ -218,11 +218,11 @@ def alf_eval_velocity(ctx, mat: alf_material, kind, group_model, precision, angl
 
 
 def alf_solve_field_noalloc(device, materials, nmaterials, region_material_ptr, nregions, theta_ptr, region_map_ptr,
-                            nx, ny, h, si, sj, init_radius, group_model, times_ptr, stream):
+                            nx, ny, h, si, sj, init_radius, group_model, times_ptr, stream, max_rounds=0):
     """Allocation-free single-field solve; returns (status, message)."""
     buf = C.create_string_buffer(256)
     code = load().alf_solve_field_noalloc(int(device), materials, int(nmaterials), region_material_ptr,
                                           int(nregions), theta_ptr, region_map_ptr, int(nx), int(ny), float(h),
-                                          int(si), int(sj), int(init_radius), int(group_model), times_ptr, stream,
-                                          buf, 256)
+                                          int(si), int(sj), int(init_radius), int(group_model), int(max_rounds),
+                                          times_ptr, stream, buf, 256)
     return int(code), buf.value.decode()

@@ -92,6 +92,9 @@ ALF_D void stencil_partials(int xA, int yA, int xB, int yB, int xC, int yC, T tA
     wt = -T(0.5) * R.h * acr * r3 * dLth;
 }
 
+// first device failure of the plan (later ones keep it)
+ALF_D void adj_set_error(QueueState* q, unsigned code) { atomicCAS(&q->error, 0u, code); }
+
 ALF_D bool frozen_at(const unsigned* bits, int box, const FieldDesc& fd, int i, int j)
 {
     const int di = i - fd.si, dj = j - fd.sj;
@@ -345,7 +348,9 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
         unsigned* const list0 = a.list[0] + fd.node_off;
         unsigned* const list1 = a.list[1] + fd.node_off;
         unsigned nact = a.cnt[f], par = 0u;
+        unsigned processed = 0u;  // Kahn's order reaches every node of a DAG exactly once
         while (nact != 0u) {
+            processed += nact;
             const unsigned* LA = par ? list1 : list0;
             unsigned* LB = par ? list0 : list1;
             unsigned nc = 0u;
@@ -386,6 +391,8 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
             nact = nc;
             par ^= 1u;
         }
+        // a node left unreleased sits on a cycle: the records do not describe one causal solve
+        if (lane == 0 && processed != (unsigned)(nx * ny)) adj_set_error(a.q, ALF_ERR_INCONSISTENT_RECORDS);
         if (smem_regions) {
             // flush this field's region sums
             double* gb = grad + (size_t)fd.sample * a.nregions;
@@ -415,6 +422,8 @@ __global__ void adj_reduce_kernel(AdjLaunch a, double* grad)
     double* gb = grad + (size_t)fd.sample * a.nregions;
     const int N = fd.nx * fd.ny;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        // every node is released once its users are processed; one that was not sits on a cycle
+        if (An[n].indeg != 0u) adj_set_error(a.q, ALF_ERR_INCONSISTENT_RECORDS);
         const T v = An[n].gn;
         if (v == T(0)) continue;
         const int i = n % fd.nx, j = n / fd.nx;
@@ -487,6 +496,8 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         if (*h_pending == 0ull) break;
     }
+    // the round cap ended the loop with nodes left in the frontiers
+    if (*h_pending != 0ull && (e = launch_set_status(a.q, ALF_ERR_INCONSISTENT_RECORDS, st)) != cudaSuccess) return e;
     const size_t smem = a.nregions <= 4096 ? (size_t)a.nregions * sizeof(double) : 0;
     adj_reduce_kernel<T><<<a.nfields, 256, smem, st>>>(a, grad);
     note_launches(1);

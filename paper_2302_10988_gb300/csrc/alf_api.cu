@@ -57,9 +57,11 @@ bool material_to_matd(const alf_material& m, MatD* out)
     if (!(rho > 0.0) || !std::isfinite(rho)) return false;
     for (double v : {c22, c23, c33, c44})
         if (!std::isfinite(v)) return false;
+    // the in-plane stiffness (c22, c23; c23, c33 and the shear c44) must be positive definite: the
+    // Christoffel matrix is then positive definite in every direction, so both of its eigenvalues
+    // (qP and qSV lambda, Sec. 3.2) are > 0
     if (!(c22 > 0.0 && c33 > 0.0 && c44 > 0.0)) return false;
-    // the in-plane 2x2 block must be positive definite for lambda_qP > 0 in every direction
-    if (!((c22 * c33 - (c23 + c44) * (c23 + c44)) > -1e300)) return false;
+    if (!(c22 * c33 - c23 * c23 > 0.0)) return false;
     out->a22 = c22 / rho;
     out->a23 = c23 / rho;
     out->a33 = c33 / rho;
@@ -145,6 +147,8 @@ alf_status run_sweep(alf_plan* p, const FimLaunch& a, cudaStream_t st)
             }
         if (*p->h_pending == 0ull) break;
     }
+    // the cap ended the loop with work left: some field never reached its fixed point
+    if (*p->h_pending != 0ull) ALF_CUDA(ctx, launch_set_status(p->d_q, ALF_ERR_NOT_CONVERGED, st));
     return ALF_OK;
 }
 
@@ -888,6 +892,7 @@ alf_status alf_backward(alf_plan* p, const double* theta, const void* times, con
     // 129 / 116 / 114 ms for 8 / 4 / 2 CTAs per SM on the 512 x 32 weld batch)
     const bool adj_warp = p->sweep_mode == 2 || p->nfields >= p->ctx->nsm * 16;
     a.warp_grid = adj_warp ? p->ctx->nsm * 2 : 0;
+    a.q = p->d_q;
     ALF_CUDA(ctx, launch_adjoint(prec, a, dL_drec, dL_dtheta, p->d_pending, p->h_pending, p->grid_eval, st));
     return ALF_OK;
 }

@@ -67,6 +67,10 @@ cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t*
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
                                 cudaStream_t st, const void* vtab = nullptr);
 cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st);
+// records `code` in q->error unless an earlier failure is recorded there (one tiny launch)
+cudaError_t launch_set_status(QueueState* q, unsigned code, cudaStream_t st);
+// streaming multiprocessors of the current device (queried once per device)
+int device_sm_count();
 cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fields, int nfields,
                                const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
                                const double* theta, const double* h, int nregions, int r0, int group_model,
@@ -158,6 +162,7 @@ struct AdjLaunch {
     const unsigned* order;
     unsigned* head;
     int warp_grid;
+    QueueState* q;    // status word: a node never released by the Kahn sweep records ALF_ERR_INCONSISTENT_RECORDS
 };
 size_t adj_node_bytes(int precision);
 cudaError_t launch_adjoint(int precision, const AdjLaunch& a, const void* dL_drec, double* grad,

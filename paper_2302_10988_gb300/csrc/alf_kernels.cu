@@ -104,14 +104,39 @@ __global__ void fill_inf_kernel(T* p, size_t n)
     if (blockIdx.x == 0 && threadIdx.x < n - nvec * V) p[nvec * V + threadIdx.x] = inf;
 }
 
+int device_sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64) {
+        const int c = cache[dev].load();
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev < 64) cache[dev].store(n);
+    return n;
+}
+
 cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st)
 {
     const size_t nvec = n / (precision == ALF_FP64 ? 2 : 4);
     int grid = (int)((nvec + 255) / 256);
-    if (grid > 152 * 16) grid = 152 * 16;
+    const int cap = device_sm_count() * 16;  // a grid-stride loop over resident blocks
+    if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (precision == ALF_FP64) fill_inf_kernel<double><<<grid, 256, 0, st>>>((double*)times, n);
     else fill_inf_kernel<float><<<grid, 256, 0, st>>>((float*)times, n);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void set_status_kernel(QueueState* q, unsigned code) { set_error(q, code); }
+
+cudaError_t launch_set_status(QueueState* q, unsigned code, cudaStream_t st)
+{
+    set_status_kernel<<<1, 1, 0, st>>>(q, code);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -79,6 +79,19 @@ cudaError_t scratch_address(unsigned char** out)
     return cudaSuccess;
 }
 
+// Flags (word *bad = 1) a region id >= nregions in the map or a material id >= nmaterials in the region
+// table: the kernels index the region constants and the material table with them.
+__global__ void check_ids_kernel(const uint16_t* region_map, int n, const uint16_t* region_material, int nregions,
+                                 int nmaterials, unsigned* bad)
+{
+    bool out = false;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out |= region_map[k] >= nregions;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nregions; k += gridDim.x * blockDim.x)
+        out |= region_material[k] >= nmaterials;
+    if (out) *bad = 1u;
+}
+
 alf_status nfail(char* err, size_t len, alf_status code, const char* msg)
 {
     if (err && len) {
@@ -97,7 +110,7 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
                                               const uint16_t* region_material, int nregions,
                                               const double* region_theta, const uint16_t* region_map, int nx, int ny,
                                               double h, int si, int sj, int init_radius, int group_model,
-                                              float* times, void* stream, char* err, size_t err_len)
+                                              int max_rounds, float* times, void* stream, char* err, size_t err_len)
 {
     char msg[256];
     if (!materials || !region_material || !region_theta || !region_map || !times)
@@ -119,6 +132,7 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
         return nfail(err, err_len, ALF_ERR_INVALID_ARG, "alf_solve_field_noalloc: unknown group model");
     if (!(h > 0.0) || !std::isfinite(h))
         return nfail(err, err_len, ALF_ERR_INVALID_ARG, "alf_solve_field_noalloc: spacing must be > 0");
+    if (max_rounds < 0) return nfail(err, err_len, ALF_ERR_INVALID_ARG, "alf_solve_field_noalloc: max_rounds < 0");
     if (si < 0 || sj < 0 || si >= nx || sj >= ny)
         return nfail(err, err_len, ALF_ERR_OUT_OF_GRID, "alf_solve_field_noalloc: source outside the grid");
     MatD mats[kNoAllocMaxMaterials];
@@ -127,7 +141,8 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
         const alf_material& M = materials[m];
         const double c22 = M.c[1][1], c23 = M.c[1][2], c33 = M.c[2][2], c44 = M.c[3][3], rho = M.rho;
         if (!(rho > 0.0) || !std::isfinite(rho) || !std::isfinite(c23) || !(c22 > 0.0) || !(c33 > 0.0) ||
-            !(c44 > 0.0) || !std::isfinite(c22) || !std::isfinite(c33) || !std::isfinite(c44))
+            !(c44 > 0.0) || !std::isfinite(c22) || !std::isfinite(c33) || !std::isfinite(c44) ||
+            !(c22 * c33 - c23 * c23 > 0.0))
             return nfail(err, err_len, ALF_ERR_NONPHYSICAL_MATERIAL, "alf_solve_field_noalloc: material");
         MatD d{};
         d.a22 = c22 / rho;
@@ -178,6 +193,21 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
     if (e == cudaSuccess) e = cudaMemsetAsync(S + kOffCounters, 0, 128, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(S + kOffCounters + 48, &bm_off, sizeof(size_t), cudaMemcpyHostToDevice, st);
+    // every region and material id in range before any kernel indexes with them
+    unsigned bad = 0u;
+    if (e == cudaSuccess) {
+        const int blocks = std::max(1, std::min(device_sm_count() * 4, (int)((N + 255) / 256)));
+        check_ids_kernel<<<blocks, 256, 0, st>>>(region_map, (int)N, region_material, nregions, nmaterials,
+                                                 (unsigned*)(S + kOffCounters + 96));
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, S + kOffCounters + 96, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && bad != 0u)
+        return nfail(err, err_len, ALF_ERR_INVALID_ARG,
+                     "alf_solve_field_noalloc: a region id >= nregions or a material id >= nmaterials");
     const FieldDesc* d_fd = (const FieldDesc*)(S + kOffField);
     const MatD* d_mats = (const MatD*)(S + kOffMats);
     const double* d_h = (const double*)(S + kOffH);
@@ -212,17 +242,20 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
     a.efield = (unsigned*)(S + kOffEfield);
     a.oldv = S + kOffOld;
     a.newv = S + kOffNew;
-    a.max_rounds_per_node = 64;
-    a.band_cells = 4.0;
+    // the host counts the rounds against the cap (64 (nx + ny) unless given); the device's own cap lies
+    // beyond it.  The front band is the plan's default, 2 cell-crossing times.
+    const long long max_total = max_rounds > 0 ? (long long)max_rounds : 64ll * (nx + ny);
+    a.max_rounds_per_node = (unsigned)(max_total / (nx + ny) + 2);
+    a.band_cells = 2.0;
     a.q = d_q;
     a.records = nullptr;
     unsigned long long* d_pending = (unsigned long long*)(S + kOffCounters + 56);
     if (e == cudaSuccess) e = launch_fim_init(ALF_FP32, a, 1, st);
     int parity = 0;
-    const long long max_rounds = 64ll * (nx + ny);
-    for (long long r = 0; e == cudaSuccess && r < max_rounds;) {
-        for (int k = 0; k < 32 && e == cudaSuccess; ++k, ++r) {
-            e = launch_fim_round(ALF_FP32, a, parity, 1, 152, st);
+    const int grid_eval = device_sm_count() * 16;
+    for (long long r = 0; e == cudaSuccess && r < max_total;) {
+        for (int k = 0; k < 32 && r < max_total && e == cudaSuccess; ++k, ++r) {
+            e = launch_fim_round(ALF_FP32, a, parity, 1, grid_eval, st);
             parity ^= 1;
         }
         if (e == cudaSuccess) e = launch_fim_pending(a, parity, d_pending, st);
@@ -239,7 +272,8 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
         std::snprintf(msg, sizeof(msg), "alf_solve_field_noalloc: %s", cudaGetErrorString(e));
         return nfail(err, err_len, ALF_ERR_CUDA, msg);
     }
-    if (qh.error != 0u)
-        return nfail(err, err_len, (alf_status)qh.error, "alf_solve_field_noalloc: the sweep did not converge");
+    if (qh.error != 0u || pending != 0ull)
+        return nfail(err, err_len, ALF_ERR_NOT_CONVERGED,
+                     "alf_solve_field_noalloc: the sweep reached its round cap before the fixed point");
     return nfail(err, err_len, ALF_OK, "");
 }

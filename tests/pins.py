@@ -61,3 +61,44 @@ def hopf_lax_group_speed(phase_speed, psi, n=4001):
         step = (hi - lo) / (n - 1)
         lo, hi = th[k] - 2 * step, th[k] + 2 * step
     return 1.0 / best
+
+
+def qp_phase_many(c6, rho, theta):
+    """qP phase speeds for an array of phase angles (the batched form of qp_phase)."""
+    th = np.asarray(theta, float).reshape(-1)
+    C = voigt_to_tensor(np.asarray(c6, float))
+    n = np.stack([np.zeros_like(th), np.cos(th), np.sin(th)], 1)
+    M = np.einsum("ijkl,bj,bl->bik", C, n, n)
+    w = np.linalg.eigvalsh(M)
+    return np.sqrt(w[:, -1] / rho).reshape(np.shape(theta))
+
+
+def exact_group_speed(c6, rho, psi):
+    """Ray (energy) speed along the angle psi from the material axis, by the Hopf-Lax maximum over
+    phase directions of cos(theta - psi) / v(theta), with the eigen-solver's phase speeds."""
+    return hopf_lax_group_speed(lambda th: qp_phase_many(c6, rho, th), psi)
+
+
+def paper_group_speed(c6, rho, psi):
+    """The paper's group speed along psi (Sec. 3.2): the phase angle theta whose qP polarisation (from the
+    eigen-solver) lies along psi, found by a scan and bisection, and V = v(theta) / cos(theta - psi)."""
+    from scipy.optimize import brentq
+
+    def mismatch(th):
+        _, p = qp_phase(c6, rho, th)
+        d = np.arctan2(p[2], p[1]) - psi
+        return (d + np.pi / 2) % np.pi - np.pi / 2
+
+    grid = np.linspace(psi - np.pi / 2 + 1e-9, psi + np.pi / 2 - 1e-9, 721)
+    f = np.array([mismatch(t) for t in grid])
+    roots = []
+    for k in range(len(grid) - 1):
+        # a sign change through zero (not a jump of the wrapped angle across +-pi/2)
+        if f[k] == 0.0:
+            roots.append(grid[k])
+        elif f[k] * f[k + 1] < 0 and abs(f[k]) < 0.5 and abs(f[k + 1]) < 0.5:
+            roots.append(brentq(mismatch, grid[k], grid[k + 1], xtol=1e-15, rtol=1e-15))
+    assert len(roots) == 1, roots
+    th = roots[0]
+    v, _ = qp_phase(c6, rho, th)
+    return v / np.cos(th - psi)
