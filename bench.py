@@ -39,16 +39,28 @@ sys.path.insert(0, ROOT)
 METRIC = "travel-time nodes/s (sources x models x nodes), batched FP32"
 WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 regions, FP32; "
             "step = solve + FP64 check + 32 rays/source + adjoint gradient")
-# algorithmic FP32-pipe operations of one evaluation of the local operator: 12 absolute values and masks,
-# 66 rank compares, 48 feasibility compares, ~181 for the stencil times and metrics of 4.9 feasible pairs
-# (37 each) and ~320 for the walk (2-3 change steps of ~100)
-OPS_PER_EVAL = 627.0
-# DRAM bytes (read + write) per evaluation of each sweep kernel, from one ncu capture of a 2,560-field
-# solve (80 weld samples x 32 sources); scaled to a launch by its evaluations.  None for a kernel that
-# changed since its capture.
-TRAFFIC_BYTES_PER_EVAL = {"fim_warp_kernel": None, "fim_cta_kernel<64>": 5.90, "fim_cta_kernel<128>": 3.31,
+# Algorithmic work of one evaluation of the local operator per node (Secs. 4.2-4.3 with the recompute rule of
+# Sec. 2): the FP64 oracle's operation count on converged fields of these workloads, stored by
+# tests/golden/make_ops_per_node.py.  The sweep's roofline divides (this count x the launch's nodes) by the
+# launch's CUDA-event time; the peak is SMs x 128 FP32 lanes x 2 (an FMA is two operations) x SM clock.
+OPS_FILE = os.path.join(ROOT, "tests", "golden", "ops_per_node.txt")
+# DRAM bytes (read + write) per node of the sweep kernel's launch, from one ncu capture of a 2,560-field solve
+# (80 weld samples x 32 sources); scaled to a launch by its nodes.  None for a kernel changed since its capture.
+TRAFFIC_BYTES_PER_NODE = {"fim_warp_kernel": None, "fim_cta_kernel<64>": None, "fim_cta_kernel<128>": None,
                           "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
+
+
+def ops_per_node(workload: str) -> float:
+    acc = [0, 0]
+    for line in open(OPS_FILE):
+        f = line.split()
+        if line.startswith("#") or len(f) != 5 or f[0] != workload:
+            continue
+        acc[0] += int(f[3])
+        acc[1] += int(f[4])
+    return acc[0] / acc[1]
 
 
 def _args():
@@ -218,6 +230,50 @@ def profile_run(args, wl, api, local):
                       "seconds": time.perf_counter() - t0}), flush=True)
 
 
+def _kernel_name(opts) -> str:
+    kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel"}[opts.sweep]
+    if opts.sweep == 3:  # the CTA shape decides how many fields share the L2, hence the traffic
+        kname += f"<{opts.cta_threads}>" + (f"x{opts.cta_cluster}" if opts.cta_cluster > 1 else "")
+    return kname
+
+
+def sweep_roofline(api, wl, theta, opts, steps, local, clock, nsm, ops_node, precision="fp32"):
+    """Roofline of the sweep kernel of a solve with the tuned options: its launches timed with CUDA events on the
+    solve's stream over `steps` solves (the library records them, option time_kernels)."""
+    Pt = api.Plan(wl, precision=precision, device=local, time_kernels=1, band_cells=opts.band_cells,
+                  sweep=opts.sweep, cta_threads=opts.cta_threads, cta_cluster=opts.cta_cluster)
+    tt = Pt.new_times()
+    Pt.solve(theta, times=tt)
+    ev_ms, evals, launches = 0.0, 0, 0
+    for _ in range(steps):
+        Pt.solve(theta, times=tt)
+        st = Pt.stats()
+        ev_ms += st["eval_ms"]
+        evals += st["evaluations"]
+        launches += st["eval_launches"]
+    if Pt.status() != 0:
+        raise SystemExit("device status non-zero in the roofline solves")
+    nodes = Pt.total_nodes
+    if precision == "fp32":
+        peak, peak_src = nsm * FP32_LANES * 2 * clock * 1e6 / 1e12, (
+            f"{nsm} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {clock:.0f} MHz (sampled SM clock)")
+    else:
+        peak, peak_src = FP64_NOMINAL_TFLOPS, "GB300 FP64 CUDA-core rate, nominal"
+    achieved = ops_node * nodes * steps / (ev_ms * 1e-3) / 1e12
+    kname = _kernel_name(opts)
+    per_launch_nodes = nodes * steps / max(launches, 1)
+    tb = TRAFFIC_BYTES_PER_NODE.get(kname)
+    out = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": tb * per_launch_nodes if tb else None,
+           "peak_source": peak_src,
+           "work": f"{ops_node:.1f} operations per node (FP64 oracle's count of one evaluation of F, "
+                   f"tests/golden/ops_per_node.txt) x {per_launch_nodes:.4g} nodes per launch",
+           "avg_launch_ms": ev_ms / max(launches, 1), "launches": launches // steps,
+           "evaluations_per_node": evals / (steps * nodes)}
+    del Pt, tt
+    return out
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -242,9 +298,12 @@ def main():
     wl = rank_workload(W, args.samples, rank)
     if args.profile:
         return profile_run(args, W.weld_single() if args.profile_workload == "plain" else wl, api, local)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    P = api.Plan(wl, precision="fp32", device=local, keep_records=1)
+    # rays: 256 points per ray is room for the longest (about 120 on a 320 x 320 grid); a ray that ran out of
+    # room would set the plan's status, which is checked
+    P = api.Plan(wl, precision="fp32", device=local, keep_records=1, max_ray_points=256)
     th = P.theta_tensor()
     times, rect, rec = P.new_times(), P.new_rec_times(), P.new_records()
     P.autotune(th, times, rec)
@@ -256,105 +315,114 @@ def main():
     stage = {}
     side = [torch.cuda.Stream(), torch.cuda.Stream()]
 
-    def step(theta, timed_stages=False):
-        if not timed_stages:
-            # after the solve, the FP64 check (FP64 pipe), the rays (FP32) and the adjoint (memory) are
-            # independent: they run on three streams and the step ends when all three have
-            P.solve(theta, times=times, rec_times=rect, records=rec)
-            solved = torch.cuda.Event()
-            solved.record(stream)
-            for s in side:
-                s.wait_event(solved)
-            with torch.cuda.stream(side[0]):
-                mr, fl = P.check64(theta, times, rec)
-            with torch.cuda.stream(side[1]):
-                P.trace_rays(theta, times)
-            g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
-            for s in side:
-                stream.wait_stream(s)
-            return mr, fl, g
+    def step(theta):
+        # after the solve, the FP64 check (FP64 pipe), the rays (FP32) and the adjoint (memory) are
+        # independent: they run on three streams and the step ends when all three have
+        cur = torch.cuda.current_stream()
+        P.solve(theta, times=times, rec_times=rect, records=rec)
+        solved = torch.cuda.Event()
+        solved.record(cur)
+        for s in side:
+            s.wait_event(solved)
+        with torch.cuda.stream(side[0]):
+            mr, fl = P.check64(theta, times, rec)
+        with torch.cuda.stream(side[1]):
+            rays = P.trace_rays(theta, times)
+        g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
+        for s in side:
+            cur.wait_stream(s)
+        return {"max_rel": mr, "flips": fl, "grad": g, "rays": rays}
+
+    def staged(theta):
         # stage timing: the same calls one after the other on one stream
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record(stream)
         P.solve(theta, times=times, rec_times=rect, records=rec)
         ev[1].record(stream)
-        mr, fl = P.check64(theta, times, rec)
+        P.check64(theta, times, rec)
         ev[2].record(stream)
         P.trace_rays(theta, times)
         ev[3].record(stream)
-        g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
+        P.backward(theta, times, rec, 2.0 * (rect - t_obs))
         ev[4].record(stream)
         torch.cuda.synchronize()
         for k, name in enumerate(["solve", "check64", "rays", "adjoint"]):
             stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
-        return mr, fl, g
 
     for _ in range(max(args.warmup, 3)):
         step(th)
+    torch.cuda.synchronize()
     if P.status() != 0:
         raise SystemExit("device status non-zero during warm-up")
 
-    # ---- timed region (headline): whole step, sweep rounds from CUDA graphs
+    # the whole step captured once in a CUDA graph (the solve is one persistent launch for the field-resident
+    # schedules, and nothing in the step waits on the host); replayed in the timed region
+    graph, out = None, None
+    launches0 = P.stats()["kernel_launches"]
+    if P.options.sweep != 1:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
+            out = step(th)
+        torch.cuda.synchronize()
+    launches = P.stats()["kernel_launches"] - launches0  # library kernels of one step
+
+    def run():
+        if graph is not None:
+            graph.replay()
+            return out
+        return step(th)
+
+    run()
+    torch.cuda.synchronize()
+    # ---- timed region (headline)
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    launches0 = P.stats()["kernel_launches"]
+    l0 = P.stats()["kernel_launches"]
     clocks.start()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for _ in range(args.steps):
-        mr, fl, g = step(th)
+        res = run()
     end.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    launches = (P.stats()["kernel_launches"] - launches0) // args.steps
+    if graph is None:
+        launches = (P.stats()["kernel_launches"] - l0) // args.steps
     ms = max_over_ranks(start.elapsed_time(end) / args.steps, world)
     if P.status() != 0:
         raise SystemExit("device status non-zero in the timed region")
+    mr, fl = res["max_rel"], res["flips"]
     nodes = P.total_nodes * world
     value = nodes / (ms * 1e-3)
     for _ in range(args.steps):
-        step(th, timed_stages=True)
+        staged(th)
     stage = {k: v / args.steps for k, v in stage.items()}
 
-    # ---- roofline of the dominant kernel (the evaluation of the local operator): its launches timed with
-    # CUDA events on the solve's stream, over a second run of the same solves
-    Pt = api.Plan(wl, precision="fp32", device=local, time_kernels=1, band_cells=P.options.band_cells,
-                  sweep=P.options.sweep, cta_threads=P.options.cta_threads, cta_cluster=P.options.cta_cluster)
-    tt = Pt.new_times()
-    Pt.solve(th, times=tt)
-    ev_ms, evals, eval_launches = 0.0, 0, 0
-    for _ in range(args.steps):
-        Pt.solve(th, times=tt)
-        s = Pt.stats()
-        ev_ms += s["eval_ms"]
-        evals += s["evaluations"]
-        eval_launches += s["eval_launches"]
+    # ---- roofline of the dominant kernel (the sweep of the local operator)
     peaks, peak_kind = _peaks()
     clock = ck["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    achieved = OPS_PER_EVAL * evals / (ev_ms * 1e-3) / 1e12
-    peak = SMS * FP32_LANES * clock * 1e6 / 1e12
-    evals_per_node = evals / (args.steps * P.total_nodes)
-    kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel"}[P.options.sweep]
-    if P.options.sweep == 3:  # the CTA shape decides how many fields share the L2, hence the traffic
-        kname += f"<{P.options.cta_threads}>" + (f"x{P.options.cta_cluster}" if P.options.cta_cluster > 1 else "")
-    del Pt, tt
+    roof = sweep_roofline(api, wl, th, P.options, args.steps, local, clock, nsm, ops_per_node("weld_batch"))
 
-    # ---- end to end through the public API: orientations from pinned host memory, receiver times back
+    # ---- end to end through the public API: orientations from pinned host memory in, receiver times, the
+    # gradient and every ray (points, point counts, times, status) back to pinned host memory
+    pts, npts, rtime, rst = res["rays"]
     th_host = torch.from_numpy(np.stack([s.region_theta for s in wl.samples])).pin_memory()
-    rt_host = torch.empty(rect.shape, dtype=rect.dtype).pin_memory()
-    g_host = torch.empty(th.shape, dtype=torch.float64).pin_memory()
+    outs = [rect, res["grad"], pts, npts, rtime, rst]
+    hosts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
     th_dev = torch.empty_like(th)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         th_dev.copy_(th_host, non_blocking=True)
-        _, _, g = step(th_dev)
-        rt_host.copy_(rect, non_blocking=True)
-        g_host.copy_(g, non_blocking=True)
+        r = step(th_dev)
+        for h, o in zip(hosts, [rect, r["grad"], *r["rays"]]):
+            h.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if P.status() != 0:
+        raise SystemExit("device status non-zero in the end-to-end steps")
 
     line = {
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
@@ -364,27 +432,21 @@ def main():
                    "rays_per_step": P.nfields * P.nrec, "band_cells": P.options.band_cells,
                    "sweep": {1: "lockstep rounds over all fields", 2: "one warp per field",
                              3: "one CTA per field"}[P.options.sweep],
+                   "cuda_graph": graph is not None,
                    "l2": "inputs larger than L2 (3.6 GB of fields), no flush"},
-        "stage_ms": stage, "evaluations_per_node": evals_per_node,
+        "stage_ms": stage, "evaluations_per_node": roof["evaluations_per_node"],
         "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},
         "e2e": {"value": nodes / (e2e_ms * 1e-3), "unit": "nodes/s",
                 "h2d_bytes_per_step": int(th_host.numel() * th_host.element_size()),
-                "d2h_bytes_per_step": int(rt_host.numel() * rt_host.element_size()
-                                          + g_host.numel() * g_host.element_size())},
-        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (TRAFFIC_BYTES_PER_EVAL[kname] * evals / args.steps / max(eval_launches // args.steps, 1)
-                                 if TRAFFIC_BYTES_PER_EVAL.get(kname) else None),
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 1 op x {clock:.0f} MHz (sampled clock); "
-                                    f"{OPS_PER_EVAL:.0f} FP32 ops per evaluation",
-                     "avg_launch_ms": ev_ms / max(eval_launches, 1), "launches": eval_launches // args.steps},
+                "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hosts))},
+        "roofline": roof,
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
         "gpu_launches": int(launches),
     }
     if not args.quick:
         # plain single-medium form: 256 x 256 weld, 32 sources
         wl1 = W.weld_single()
-        plain = {}
+        plain, plain_roof = {}, {}
         for prec in ("fp32", "fp64"):
             P1 = api.Plan(wl1, precision=prec, device=local)
             th1 = P1.theta_tensor()
@@ -401,8 +463,11 @@ def main():
             plain[prec] = P1.total_nodes / (e0.elapsed_time(e1) / 3 * 1e-3)
             plain[prec + "_schedule"] = {"sweep": P1.options.sweep, "band_cells": P1.options.band_cells,
                                          "cta_threads": P1.options.cta_threads}
+            plain_roof[prec] = sweep_roofline(api, wl1, th1, P1.options, 3, local, clock, nsm,
+                                              ops_per_node("weld_single"), prec)
             del P1, t1
         line["plain_nodes_per_s"] = plain
+        line["plain_roofline"] = plain_roof
         # large single medium: 2048 x 2048, 64 sources, 4096 receivers per source
         wlL = W.weld_large()
         PL = api.Plan(wlL, precision="fp32", device=local, max_ray_points=1024)

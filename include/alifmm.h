@@ -135,6 +135,15 @@ typedef struct {
                                as many SMs, 1, 2, 4 or 8; 0 = choose (default): for FP32 batches with no more
                                fields than SMs, the largest that keeps fields x cluster <= SMs and leaves at
                                least 2^19 nodes of the largest field per SM, else 1 */
+    int subgrid;            /* global sub-grid size s (Sec. 4.5, Table 2; Sec. 5.1), odd, 1..21 (default 1):
+                               the plan solves every sample on its grid refined s times in each direction,
+                               (nx - 1) s + 1 by (ny - 1) s + 1 nodes of spacing h / s, each fine node taking
+                               the region of the nearest original node; sources and receivers sit at the
+                               fine nodes (i s, j s).  Fields, records, ray points and every field offset are
+                               those of the fine grid; the original nodes are every s-th fine node.
+                               init_radius, level_radius, plane_step, ray_halfwidth and stop_radius stay in
+                               original cells (the plan multiplies them by s); level_density is relative to
+                               the fine grid. */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */
@@ -146,8 +155,15 @@ void alf_default_options(alf_options* opt);
  *  nx[b], ny[b]   grid size of sample b, 2..16384 each, nx*ny <= 2^28
  *  h[b]           node spacing of sample b (m), > 0
  *  region_map     uint16 region id per node, samples packed back to back,
- *                 sample b is [ny[b]][nx[b]]
- *  region_material[r]  material index of region r (< nmaterials)
+ *                 sample b is [ny[b]][nx[b]]; may be NULL when region_map32 is given
+ *  region_map32   the same with uint32 ids, for more than 65,536 regions (a
+ *                 per-node orientation map is nregions = nx*ny with region id
+ *                 = node index); used instead of region_map when not NULL
+ *  nregions       1..2^28, with nsamples * nregions <= 2^30
+ *  region_material[r]  material index of region r (< nmaterials); may be NULL when region_material32 is given
+ *  region_material32    the same with uint32 indices, for more than 65,536 materials (a per-node stiffness
+ *                 map is one material per region); used instead of region_material when not NULL
+ *  nmaterials     1..2^28 (velocity_table: at most 65,536)
  *  src_ij[b][s][2], rec_ij[b][r][2]  (i, j) nodes, inside the sample's grid */
 typedef struct {
     int nsamples;
@@ -163,6 +179,8 @@ typedef struct {
     const int32_t* src_ij;
     int nreceivers;
     const int32_t* rec_ij;
+    const uint32_t* region_map32;
+    const uint32_t* region_material32;
 } alf_geometry;
 
 typedef struct alf_ctx alf_ctx;
@@ -227,6 +245,20 @@ alf_status alf_solve(alf_plan* plan, const double* region_theta, void* times, vo
  *  n_flips      [nfields] int32, output (0 when records is NULL) */
 alf_status alf_check64(alf_plan* plan, const double* region_theta, const void* times, const uint8_t* records,
                        double* max_rel, int32_t* n_flips, void* stream);
+
+/* The same FP64 check, also returning every node's FP64 value and stencil
+ * record (for node-by-node comparison with a reference evaluation):
+ *  check_times    [total nodes] double, output: U(S_D) in FP64, where S_D is
+ *                 the node's frozen neighbours and those whose key (tau,
+ *                 index) precedes its own; frozen nodes and nodes without a
+ *                 value keep their time; may be NULL
+ *  check_records  [total nodes] uint8, output: the record of that value
+ *                 (codes as in alf_solve; 254 frozen, 255 none); may be NULL
+ *                 (not both)
+ * Other arguments as alf_check64. */
+alf_status alf_check64_nodes(alf_plan* plan, const double* region_theta, const void* times, const uint8_t* records,
+                             double* check_times, uint8_t* check_records, double* max_rel, int32_t* n_flips,
+                             void* stream);
 
 /* Ray tracing (Sec. 5.1) for every (sample, source, receiver): the ray starts
  * at the receiver and walks plane by plane to the source through the source's
@@ -307,7 +339,7 @@ alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, in
  * synchronise the device, are not allowed).  It runs the lockstep-round
  * kernels of alf_solve (sweep 1) in FP32 with the radius initialisation and
  * the plan's default front band (2 cell-crossing times), but keeps every
- * workspace in a fixed device array inside the library (about 7 MB per GPU
+ * workspace in a fixed device array inside the library (about 8 MB per GPU
  * that loads the library, held until the process exits).
  * Limits: nx*ny <= 512*512 nodes, nregions <= 1024, nmaterials <= 64,
  * init_radius <= 8; larger inputs are rejected with ALF_ERR_INVALID_ARG and a

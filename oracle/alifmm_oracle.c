@@ -55,8 +55,16 @@ typedef struct {
 static int64_t g_root_swaps = 0;     /* [R1] times the printed root failed the qP check */
 static int64_t g_disc_clamps = 0;    /* negative discriminant clamped to zero */
 
-int64_t om_counter(int which) { return which == 0 ? g_root_swaps : g_disc_clamps; }
-void om_reset_counters(void) { g_root_swaps = 0; g_disc_clamps = 0; }
+/* Operation count of the local update (stencil times, metrics, the choice, the ordering of the
+ * neighbours, the fallback): every floating-point add, subtract, multiply, divide, square root,
+ * absolute value, comparison and libm call the code below executes counts 1.  The fallback's group
+ * speed along a diamond direction depends only on the material and orientation of D, not on the
+ * field, so a fallback candidate counts as its add and its comparison (2); group speeds themselves
+ * are not counted.  The count gives the algorithmic work per node evaluation of a solve. */
+static int64_t g_ops = 0;
+
+int64_t om_counter(int which) { return which == 0 ? g_root_swaps : which == 1 ? g_disc_clamps : g_ops; }
+void om_reset_counters(void) { g_root_swaps = 0; g_disc_clamps = 0; g_ops = 0; }
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 3.1-3.2: velocities                                                   */
@@ -278,6 +286,8 @@ static double stencil_time(const om_medium* M, int d, const double xa[3], const 
 {
     double xA = xa[0], yA = ya[0], xB = xa[1], yB = ya[1], xC = xa[2], yC = ya[2];
     double xD = 0.0, yD = 0.0;
+    /* a 3, E 8, |FD| 15, theta_n 3, theta' 4, v 26 (isotropic: 2), tau_D 3 */
+    g_ops += mat_is_isotropic(&M->mats[M->mat_id[d]]) ? 38 : 62;
     double a = (tB - tA) / (tC - tA);
     double xE = (1.0 - a) * xA + a * xC;
     double yE = (1.0 - a) * yA + a * yC;
@@ -353,6 +363,7 @@ static double update_from_set(const om_medium* M, int i, int j, const int known[
             }
             if (!ok) continue;
             double tA = t[slot[0]], tB = t[slot[1]], tC = t[slot[2]];
+            g_ops += tA < tB ? 2 : 1;
             if (!(tA < tB && tB <= tC)) continue;
             double metric;
             if (pass == 0) {
@@ -364,7 +375,9 @@ static double update_from_set(const om_medium* M, int i, int j, const int known[
                 metric = fabs(tdiag - ((sqrt(2.0) - 1.0) * tA + (2.0 - sqrt(2.0)) * taxis));
             }
             double xa[3] = {s[0], s[2], s[4]}, ya[3] = {s[1], s[3], s[5]};
+            g_ops += pass == 0 ? 2 : 5;         /* the metric */
             double val = stencil_time(M, d, xa, ya, tA, tB, tC);
+            g_ops += 2;                          /* [R17] and the choice */
             if (!(val > tC)) continue; /* [R17] */
             if (metric < best_metric) {
                 best_metric = metric;
@@ -387,6 +400,7 @@ static double update_from_set(const om_medium* M, int i, int j, const int known[
         double len = sqrt(di * di + dj * dj);
         double V = om_group_speed(m, M->group_model, atan2(dj, di), M->theta[d]);
         double val = t[k] + len * M->h / V;
+        g_ops += 2;
         if (val < best) {
             best = val;
             bk = k;
@@ -605,6 +619,7 @@ double om_F_node(const om_medium* M, const uint8_t* frozen, const double* tau, i
         while (b >= 0) {
             int kb = cand[b];
             int nb = (j + DIAMOND[kb][1]) * nx + i + DIAMOND[kb][0];
+            g_ops += t[kb] > t[k] ? 1 : 2;
             if (t[kb] > t[k] || (t[kb] == t[k] && nb > nk)) {
                 cand[b + 1] = cand[b];
                 --b;
@@ -619,6 +634,7 @@ double om_F_node(const om_medium* M, const uint8_t* frozen, const double* tau, i
         if (kk == nc) break;
         int k = cand[kk];
         int nk = (j + DIAMOND[k][1]) * nx + i + DIAMOND[k][0];
+        g_ops += u < t[k] ? 1 : 2;
         if (u < t[k] || (u == t[k] && d < nk)) break; /* D precedes the next neighbour */
         known[k] = 1;
         u = update_from_set(M, i, j, known, t, &urec);
@@ -792,6 +808,9 @@ int om_trace_ray(const om_medium* M, const double* tau, double x0, double y0, do
     int np = 0;
     int cap = o->max_pts;
     double bx = x0, by = y0, dx = xt - x0, dy = yt - y0;
+    /* the candidates of one plane: at most 2 halfwidth + 1 nodes */
+    double* cost = (double*)malloc(sizeof(double) * (size_t)(2 * o->halfwidth + 1));
+    int* pidx = (int*)malloc(sizeof(int) * (size_t)(2 * o->halfwidth + 1));
     pts[2 * np] = bx;
     pts[2 * np + 1] = by;
     np++;
@@ -866,8 +885,6 @@ int om_trace_ray(const om_medium* M, const double* tau, double x0, double y0, do
         }
         int plo = p0 - o->halfwidth, phi = p0 + o->halfwidth;
         /* clip to nodes inside the grid */
-        double cost[64];
-        int pidx[64];
         int nc = 0;
         for (int p = plo; p <= phi; ++p) {
             double cx = bxn + p * tx, cy = byn + p * ty;
@@ -910,6 +927,8 @@ int om_trace_ray(const om_medium* M, const double* tau, double x0, double y0, do
         pts[2 * np + 1] = by;
         np++;
     }
+    free(cost);
+    free(pidx);
     *npts_out = np;
     return status;
 }

@@ -227,6 +227,18 @@ def F_check(M: OMedium, frozen, tau):
     return tout.reshape(M.ny, M.nx), rec.reshape(M.ny, M.nx)
 
 
+def ops_of_F_all(M: OMedium, frozen, tau):
+    """Operations (the count defined in the C file) of one evaluation of F at every non-frozen node of a
+    solved field, and the number of those nodes."""
+    L = lib()
+    L.om_reset_counters()
+    F_all(M, frozen, tau)
+    n = int(np.count_nonzero(np.asarray(frozen).reshape(-1) == 0))
+    ops = int(L.om_counter(2))
+    L.om_reset_counters()
+    return ops, n
+
+
 def jacobi(M: OMedium, frozen, tau0, max_iter=100000):
     frozen = np.ascontiguousarray(frozen, np.uint8).reshape(-1)
     tau = np.ascontiguousarray(tau0, np.float64).reshape(-1).copy()

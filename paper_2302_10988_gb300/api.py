@@ -42,7 +42,9 @@ class Plan:
     Keyword options map to ``alf_options`` fields (precision "fp32"/"fp64",
     group "paper"/"exact", init_mode, init_radius, n_levels, level_density, level_radius,
     plane_step, ray_halfwidth, ray_family, stop_radius, max_ray_points, max_rounds, sweep, keep_records,
-    band_cells, use_graph, time_kernels, velocity_table, cta_threads, cta_cluster); array fields take a sequence of 4 ints."""
+    band_cells, use_graph, time_kernels, velocity_table, cta_threads, cta_cluster, subgrid); array fields take a
+    sequence of 4 ints.  With subgrid s > 1 every field, record and ray lives on the grid refined s times
+    (``shapes`` are the fine grids; the original nodes are every s-th fine node)."""
 
     def __init__(self, wl, precision="fp32", group="paper", device=0, **opts):
         self.wl = wl
@@ -69,8 +71,12 @@ class Plan:
         nx = np.array([s.nx for s in wl.samples], np.int32)
         ny = np.array([s.ny for s in wl.samples], np.int32)
         h = np.array([s.h for s in wl.samples], np.float64)
-        rmap = np.ascontiguousarray(np.concatenate([s.region_map.astype(np.uint16).ravel() for s in wl.samples]))
-        rmat = np.ascontiguousarray(wl.region_material.astype(np.uint16))
+        # 16-bit region ids while they fit, else 32-bit ones (per-node orientation maps)
+        wide = wl.nregions > 65536 or any(s.region_map.dtype.itemsize > 2 for s in wl.samples)
+        rmap = np.ascontiguousarray(np.concatenate([s.region_map.astype(np.uint32 if wide else np.uint16).ravel()
+                                                    for s in wl.samples]))
+        wide_mat = len(wl.materials) > 65536
+        rmat = np.ascontiguousarray(wl.region_material.astype(np.uint32 if wide_mat else np.uint16))
         mats = (B.alf_material * len(wl.materials))(*[_material(c6, rho) for c6, rho in wl.materials])
         src = np.ascontiguousarray(np.stack([s.src for s in wl.samples]).astype(np.int32))
         rec = np.ascontiguousarray(np.stack([s.rec for s in wl.samples]).astype(np.int32)) if Rr else \
@@ -80,14 +86,18 @@ class Plan:
         def ptr(a, t):
             return a.ctypes.data_as(C.POINTER(t))
         g = B.alf_geometry(len(wl.samples), ptr(nx, C.c_int32), ptr(ny, C.c_int32), ptr(h, C.c_double),
-                           ptr(rmap, C.c_uint16), wl.nregions, ptr(rmat, C.c_uint16), len(wl.materials), mats, S,
-                           ptr(src, C.c_int32), Rr, ptr(rec, C.c_int32))
+                           None if wide else ptr(rmap, C.c_uint16), wl.nregions,
+                           None if wide_mat else ptr(rmat, C.c_uint16), len(wl.materials), mats, S,
+                           ptr(src, C.c_int32), Rr, ptr(rec, C.c_int32), ptr(rmap, C.c_uint32) if wide else None,
+                           ptr(rmat, C.c_uint32) if wide_mat else None)
         self.plan = B.alf_plan_create(self.ctx, g, o)
         self.options = B.alf_plan_options(self.plan)
         self.nfields = B.alf_plan_nfields(self.plan)
         self.offsets = [B.alf_plan_field_offset(self.plan, f) for f in range(self.nfields + 1)]
         self.total_nodes = self.offsets[-1]
-        self.shapes = [(s.ny, s.nx) for s in wl.samples for _ in range(S)]
+        sg = max(1, int(self.options.subgrid))
+        self.subgrid = sg
+        self.shapes = [((s.ny - 1) * sg + 1, (s.nx - 1) * sg + 1) for s in wl.samples for _ in range(S)]
 
     def __del__(self):
         try:
@@ -142,6 +152,19 @@ class Plan:
                       C.c_void_p(records.data_ptr()) if records is not None else None,
                       C.c_void_p(max_rel.data_ptr()), C.c_void_p(flips.data_ptr()), self._stream())
         return max_rel, flips
+
+    def check64_nodes(self, theta, times, records=None):
+        """The FP64 check with every node's FP64 value and record: (check_times float64, check_records uint8,
+        max_rel, flips)."""
+        max_rel = torch.empty(self.nfields, dtype=torch.float64, device=self._dev())
+        flips = torch.empty(self.nfields, dtype=torch.int32, device=self._dev())
+        ct = torch.empty(self.total_nodes, dtype=torch.float64, device=self._dev())
+        cr = torch.empty(self.total_nodes, dtype=torch.uint8, device=self._dev())
+        B.alf_check64_nodes(self.ctx, self.plan, C.c_void_p(theta.data_ptr()), C.c_void_p(times.data_ptr()),
+                            C.c_void_p(records.data_ptr()) if records is not None else None,
+                            C.c_void_p(ct.data_ptr()), C.c_void_p(cr.data_ptr()), C.c_void_p(max_rel.data_ptr()),
+                            C.c_void_p(flips.data_ptr()), self._stream())
+        return ct, cr, max_rel, flips
 
     def trace_rays(self, theta, times):
         P = self.options.max_ray_points

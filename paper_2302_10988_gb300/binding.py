@@ -26,7 +26,7 @@ ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
 EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error", "alf_plan_create",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
            "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats", "alf_plan_autotune",
-           "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient")
+           "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient", "alf_check64_nodes")
 
 
 class AlfError(RuntimeError):
@@ -46,7 +46,7 @@ class alf_options(C.Structure):
                 ("max_ray_points", C.c_int), ("max_rounds", C.c_int), ("sweep", C.c_int),
                 ("ray_family", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double),
                 ("use_graph", C.c_int), ("time_kernels", C.c_int), ("velocity_table", C.c_int),
-                ("cta_threads", C.c_int), ("cta_cluster", C.c_int)]
+                ("cta_threads", C.c_int), ("cta_cluster", C.c_int), ("subgrid", C.c_int)]
 
 
 class alf_stats(C.Structure):
@@ -59,7 +59,8 @@ class alf_geometry(C.Structure):
                 ("h", C.POINTER(C.c_double)), ("region_map", C.POINTER(C.c_uint16)), ("nregions", C.c_int),
                 ("region_material", C.POINTER(C.c_uint16)), ("nmaterials", C.c_int),
                 ("materials", C.POINTER(alf_material)), ("nsources", C.c_int), ("src_ij", C.POINTER(C.c_int32)),
-                ("nreceivers", C.c_int), ("rec_ij", C.POINTER(C.c_int32))]
+                ("nreceivers", C.c_int), ("rec_ij", C.POINTER(C.c_int32)),
+                ("region_map32", C.POINTER(C.c_uint32)), ("region_material32", C.POINTER(C.c_uint32))]
 
 
 _lib = None
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
         L.alf_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         L.alf_check64.restype = C.c_int
         L.alf_check64.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.alf_check64_nodes.restype = C.c_int
+        L.alf_check64_nodes.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.alf_trace_rays.restype = C.c_int
         L.alf_trace_rays.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.alf_ray_gradient.restype = C.c_int
@@ -180,6 +183,12 @@ def alf_solve(ctx, plan, theta_ptr, times_ptr, rec_ptr, records_ptr, stream):
 
 def alf_check64(ctx, plan, theta_ptr, times_ptr, records_ptr, max_rel_ptr, flips_ptr, stream):
     _check(ctx, load().alf_check64(plan, theta_ptr, times_ptr, records_ptr, max_rel_ptr, flips_ptr, stream))
+
+
+def alf_check64_nodes(ctx, plan, theta_ptr, times_ptr, records_ptr, ctimes_ptr, crec_ptr, max_rel_ptr, flips_ptr,
+                      stream):
+    _check(ctx, load().alf_check64_nodes(plan, theta_ptr, times_ptr, records_ptr, ctimes_ptr, crec_ptr, max_rel_ptr,
+                                         flips_ptr, stream))
 
 
 def alf_trace_rays(ctx, plan, theta_ptr, times_ptr, pts_ptr, npts_ptr, time_ptr, status_ptr, stream):

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
         const int nx = fd.nx, ny = fd.ny;
         AdjNode<T>* const An = A + fd.node_off;
         const unsigned* fbits = a.frozen_bits + (size_t)f * frozen_words(a.box);
-        const uint16_t* map = a.region_map + fd.map_off;
+        const uint32_t* map = a.region_map + fd.map_off;
         const int rsrc = map[(long long)fd.sj * nx + fd.si];
         unsigned* const list0 = a.list[0] + fd.node_off;
         unsigned* const list1 = a.list[1] + fd.node_off;

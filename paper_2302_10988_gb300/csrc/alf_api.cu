@@ -193,6 +193,7 @@ void alf_default_options(alf_options* o)
     o->band_cells = 2.0;
     o->use_graph = 1;
     o->time_kernels = 0;
+    o->subgrid = 1;
 }
 
 alf_status alf_create(alf_ctx** out, int cuda_device)
@@ -304,8 +305,6 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
                 return fail(ctx, ALF_ERR_INVALID_ARG, "level densities must be odd, >= 3, each dividing the previous");
             if (r < 1 || r > 16 || (l > 0 && r <= opt.level_radius[l - 1]))
                 return fail(ctx, ALF_ERR_INVALID_ARG, "level radii must increase within 1..16");
-            if ((2 * r * d + 1) * (2 * r * d + 1) > (1 << 16))
-                return fail(ctx, ALF_ERR_INVALID_ARG, "level %d grid too large (%d^2 nodes)", l, 2 * r * d + 1);
         }
     } else {
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
@@ -326,20 +325,103 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
         return fail(ctx, ALF_ERR_INVALID_ARG, "ray options out of range");
+    if (opt.subgrid == 0) opt.subgrid = 1;  // a zeroed options struct means no refinement
+    if (opt.subgrid < 1 || opt.subgrid > 21 || opt.subgrid % 2 == 0)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "subgrid must be an odd number in 1..21");
+    const alf_options opt_caller = opt;
+    const int sg = opt.subgrid;
+    // lengths given in original cells become fine cells
+    opt.init_radius *= sg;
+    for (int l = 0; l < 4; ++l) opt.level_radius[l] *= sg;
+    opt.plane_step *= sg;
+    opt.ray_halfwidth *= sg;
+    opt.stop_radius *= sg;
+    if (opt.init_mode == ALF_INIT_HIERARCHY)
+        for (int l = 0; l < opt.n_levels; ++l) {
+            const long long side = 2ll * opt.level_radius[l] * opt.level_density[l] + 1;
+            if (side * side > (1 << 16))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "level %d grid too large (%lld^2 nodes)", l, side);
+        }
     // ---- geometry
-    if (g->nsamples < 1 || g->nregions < 1 || g->nregions > 65536 || g->nmaterials < 1 || g->nmaterials > 65536 ||
-        g->nsources < 1 || g->nreceivers < 0)
+    if (g->nsamples < 1 || g->nregions < 1 || g->nregions > (1 << 28) || g->nmaterials < 1 ||
+        g->nmaterials > (1 << 28) || g->nsources < 1 || g->nreceivers < 0 ||
+        (long long)g->nsamples * g->nregions > (1ll << 30))
         return fail(ctx, ALF_ERR_INVALID_ARG, "geometry counts out of range");
-    if (!g->nx || !g->ny || !g->h || !g->region_map || !g->region_material || !g->materials || !g->src_ij ||
+    if (!g->nx || !g->ny || !g->h || (!g->region_map && !g->region_map32) ||
+        (!g->region_material && !g->region_material32) || !g->materials || !g->src_ij ||
         (g->nreceivers > 0 && !g->rec_ij))
         return fail(ctx, ALF_ERR_INVALID_ARG, "geometry has a null array");
+    if (!g->region_map32 && g->nregions > 65536)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "more than 65536 regions need region_map32");
+    if (!g->region_material32 && g->nmaterials > 65536)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "more than 65536 materials need region_material32");
+    if (opt.velocity_table && g->nmaterials > 65536)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table: at most 65536 materials");
+    std::vector<uint32_t> rmat32(g->nregions);
+    for (int r = 0; r < g->nregions; ++r)
+        rmat32[r] = g->region_material32 ? g->region_material32[r] : g->region_material[r];
+    // region ids as 32-bit values (the device map's type), samples back to back
+    std::vector<uint32_t> map32;
+    {
+        size_t total = 0;
+        for (int b = 0; b < g->nsamples; ++b) {
+            const long long nx = g->nx[b], ny = g->ny[b];
+            if (nx < 2 || ny < 2 || nx > 16384 || ny > 16384 || nx * ny > (1ll << 28))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: grid %lldx%lld out of range", b, nx, ny);
+            total += (size_t)(nx * ny);
+        }
+        map32.resize(total);
+        for (size_t k = 0; k < total; ++k) map32[k] = g->region_map32 ? g->region_map32[k] : g->region_map[k];
+    }
+    // global sub-grid (Sec. 4.5): every sample refined sg times, fine nodes taking the region of the nearest
+    // original node (unique for odd sg), sources and receivers on the fine nodes of the original ones
+    std::vector<int32_t> fnx, fny, fsrc, frec;
+    std::vector<double> fh;
+    std::vector<uint32_t> fmap;
+    alf_geometry gfine;
+    if (sg > 1) {
+        size_t fine_total = 0;
+        for (int b = 0; b < g->nsamples; ++b) {
+            const long long nx = g->nx[b], ny = g->ny[b];
+            if (nx < 2 || ny < 2 || (nx - 1) * sg + 1 > 16384 || (ny - 1) * sg + 1 > 16384 ||
+                ((nx - 1) * sg + 1) * ((ny - 1) * sg + 1) > (1ll << 28))
+                return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: grid %lldx%lld out of range with subgrid %d", b, nx,
+                            ny, sg);
+            fine_total += (size_t)((nx - 1) * sg + 1) * (size_t)((ny - 1) * sg + 1);
+        }
+        fmap.resize(fine_total);
+        size_t off = 0, src_off = 0;
+        for (int b = 0; b < g->nsamples; ++b) {
+            const int nx = g->nx[b], ny = g->ny[b], nxf = (nx - 1) * sg + 1, nyf = (ny - 1) * sg + 1;
+            fnx.push_back(nxf);
+            fny.push_back(nyf);
+            fh.push_back(g->h[b] / sg);
+            for (int j = 0; j < nyf; ++j) {
+                const int oj = (2 * j + sg) / (2 * sg);  // nearest original row
+                for (int i = 0; i < nxf; ++i)
+                    fmap[off + (size_t)j * nxf + i] = map32[src_off + (size_t)oj * nx + (2 * i + sg) / (2 * sg)];
+            }
+            off += (size_t)nxf * nyf;
+            src_off += (size_t)nx * ny;
+        }
+        for (size_t k = 0; k < (size_t)g->nsamples * g->nsources * 2; ++k) fsrc.push_back(g->src_ij[k] * sg);
+        for (size_t k = 0; k < (size_t)g->nsamples * g->nreceivers * 2; ++k) frec.push_back(g->rec_ij[k] * sg);
+        gfine = *g;
+        gfine.nx = fnx.data();
+        gfine.ny = fny.data();
+        gfine.h = fh.data();
+        map32.swap(fmap);
+        gfine.src_ij = fsrc.data();
+        gfine.rec_ij = g->nreceivers > 0 ? frec.data() : nullptr;
+        g = &gfine;
+    }
     std::vector<MatD> mats(g->nmaterials);
     for (int m = 0; m < g->nmaterials; ++m)
         if (!material_to_matd(g->materials[m], &mats[m]))
             return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "material %d: rho <= 0, non-finite or non-positive c", m);
     for (int r = 0; r < g->nregions; ++r)
-        if (g->region_material[r] >= g->nmaterials)
-            return fail(ctx, ALF_ERR_INVALID_ARG, "region %d refers to material %d of %d", r, g->region_material[r],
+        if (rmat32[r] >= (uint32_t)g->nmaterials)
+            return fail(ctx, ALF_ERR_INVALID_ARG, "region %d refers to material %u of %d", r, rmat32[r],
                         g->nmaterials);
 
     alf_plan* p = new (std::nothrow) alf_plan();
@@ -365,10 +447,9 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
             return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: spacing must be > 0", b);
         }
         for (size_t k = 0; k < (size_t)nx * ny; ++k)
-            if (g->region_map[map_off + k] >= g->nregions) {
+            if (map32[map_off + k] >= (uint32_t)g->nregions) {
                 delete p;
-                return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: region id %d >= nregions", b,
-                            g->region_map[map_off + k]);
+                return fail(ctx, ALF_ERR_INVALID_ARG, "sample %d: region id %u >= nregions", b, map32[map_off + k]);
             }
         for (int s = 0; s < p->S; ++s) {
             const int si = g->src_ij[((size_t)b * p->S + s) * 2], sj = g->src_ij[((size_t)b * p->S + s) * 2 + 1];
@@ -394,9 +475,11 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // fastest qP speed over the materials (scan of phase angles; the group speed at the
     // same point of the wavefront is never below it, so this bounds the fastest front)
     double vmax = 0.0;
+    // (a coarser scan when every node has its own material: the bound only sets the band width)
+    const int nang = mats.size() > 4096 ? 36 : 180;
     for (const MatD& m : mats)
-        for (int k = 0; k < 180; ++k) {
-            const double th = k * 3.141592653589793 / 180.0, c = std::cos(th), sn = std::sin(th);
+        for (int k = 0; k < nang; ++k) {
+            const double th = k * 3.141592653589793 / nang, c = std::cos(th), sn = std::sin(th);
             double lam = m.a22;
             if (!m.iso) {
                 const double al = c * c * m.a22 + sn * sn * m.a44, ga = c * c * m.a44 + sn * sn * m.a33;
@@ -466,6 +549,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     }
     p->bm_words = bm_words;
     p->opt = opt;
+    p->opt_caller = opt_caller;
 
     cudaSetDevice(ctx->device);
     const size_t rsz = opt.precision == ALF_FP64 ? sizeof(RegionP<double>) : sizeof(RegionP<float>);
@@ -571,9 +655,9 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         });
         if (e == cudaSuccess) e = up(p->d_order, order.data(), order.size() * sizeof(unsigned));
     }
-    if (e == cudaSuccess) e = up(p->d_map, g->region_map, p->total_map * sizeof(uint16_t));
+    if (e == cudaSuccess) e = up(p->d_map, map32.data(), p->total_map * sizeof(uint32_t));
     if (e == cudaSuccess) e = up(p->d_bm_off, bm_off.data(), bm_off.size() * sizeof(size_t));
-    if (e == cudaSuccess) e = up(p->d_region_mat, g->region_material, (size_t)p->R * sizeof(uint16_t));
+    if (e == cudaSuccess) e = up(p->d_region_mat, rmat32.data(), (size_t)p->R * sizeof(uint32_t));
     if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
     if (e == cudaSuccess && opt.velocity_table) {
         // phase speed of every material at 0..180 degrees from its axis (the qP eigenvalue of the rotated
@@ -635,7 +719,9 @@ int alf_plan_nfields(const alf_plan* p) { return p ? p->nfields : 0; }
 alf_status alf_plan_options(const alf_plan* p, alf_options* out)
 {
     if (!p || !out) return ALF_ERR_INVALID_ARG;
-    *out = p->opt;
+    // lengths as the caller gave them (original cells); the schedule and band in effect
+    *out = p->opt_caller;
+    out->band_cells = p->opt.band_cells;
     out->sweep = p->sweep_mode;
     out->cta_threads = p->cta_threads;
     out->cta_cluster = p->cta_cluster;
@@ -763,6 +849,24 @@ alf_status alf_check64(alf_plan* p, const double* theta, const void* times, cons
     ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
                                  records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st,
                                  p->opt.velocity_table));
+    return ALF_OK;
+}
+
+alf_status alf_check64_nodes(alf_plan* p, const double* theta, const void* times, const uint8_t* records,
+                             double* check_times, uint8_t* check_records, double* max_rel, int32_t* n_flips,
+                             void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times || !max_rel || !n_flips || (!check_times && !check_records))
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_check64_nodes: null pointer");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = as_stream(stream);
+    ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R,
+                                      p->opt.group_model, p->d_regions64, st, p->d_vtab64));
+    ALF_CUDA(ctx, launch_check64(p->opt.precision, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R,
+                                 records, p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st,
+                                 p->opt.velocity_table, check_times, check_records));
     return ALF_OK;
 }
 

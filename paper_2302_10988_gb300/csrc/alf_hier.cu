@@ -35,7 +35,7 @@ template <typename T>
 struct HierScratch {
     T* tcur;
     T* tprev;
-    uint16_t* map;
+    uint32_t* map;
     unsigned* kprev;  // known bitmap of the previous level
     unsigned* list0;
     unsigned* list1;
@@ -47,7 +47,7 @@ struct HierScratch {
 template <typename T>
 ALF_D HierScratch<T> carve(void* base, size_t L)
 {
-    // T arrays first (aligned to their size), then 32-bit arrays, then the 16-bit map
+    // T arrays first (aligned to their size), then the 32-bit arrays and the map
     char* p = (char*)base;
     HierScratch<T> s;
     s.tcur = (T*)p;
@@ -66,7 +66,7 @@ ALF_D HierScratch<T> carve(void* base, size_t L)
     p += L * 4;
     s.kprev = (unsigned*)p;
     p += ((L + 31) / 32) * 4;
-    s.map = (uint16_t*)p;
+    s.map = (uint32_t*)p;
     return s;
 }
 
@@ -75,7 +75,7 @@ ALF_D HierScratch<T> carve(void* base, size_t L)
 size_t hier_scratch_bytes(int precision, size_t L)
 {
     const size_t tb = precision == ALF_FP64 ? 8 : 4;
-    const size_t bytes = 4 * L * tb + 3 * L * 4 + ((L + 31) / 32) * 4 + L * 2;
+    const size_t bytes = 4 * L * tb + 3 * L * 4 + ((L + 31) / 32) * 4 + L * 4;
     return (bytes + 255) / 256 * 256;
 }
 
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) hier_kernel(HierLaunch a)
         if (f >= (unsigned)a.nfields || err != 0u) return;
         const FieldDesc fd = a.fields[f];
         const int nx = fd.nx, ny = fd.ny, si = fd.si, sj = fd.sj;
-        const uint16_t* omap = a.region_map + fd.map_off;
+        const uint32_t* omap = a.region_map + fd.map_off;
         const int rsrc = omap[(long long)sj * nx + si];
         const MatD msrc = a.mats[a.region_mat[rsrc]];
         const double th_src = a.theta[(size_t)fd.sample * a.nregions + rsrc];

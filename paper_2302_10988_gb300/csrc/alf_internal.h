@@ -37,7 +37,7 @@ struct FimLaunch {
     void* times;
     const FieldDesc* fields;
     int nfields;
-    const uint16_t* region_map;
+    const uint32_t* region_map;
     const void* regions;  // RegionP<T>[nsamples][nregions]
     int nregions;
     int box;                       // half-width of the frozen box around each source
@@ -63,7 +63,7 @@ struct FimLaunch {
 // kernels (alf_kernels.cu)
 // velocity table: the qP phase speed at 0, 1, ..., 180 degrees from the material axis, per material
 #define ALF_VTAB_N 181
-cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t* region_mat, const double* theta,
+cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint32_t* region_mat, const double* theta,
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
                                 cudaStream_t st, const void* vtab = nullptr);
 cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st);
@@ -72,7 +72,7 @@ cudaError_t launch_set_status(QueueState* q, unsigned code, cudaStream_t st);
 // streaming multiprocessors of the current device (queried once per device)
 int device_sm_count();
 cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fields, int nfields,
-                               const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
+                               const uint32_t* region_map, const uint32_t* region_mat, const MatD* mats,
                                const double* theta, const double* h, int nregions, int r0, int group_model,
                                unsigned* frozen_bits, int box, cudaStream_t st);
 cudaError_t launch_fim_init(int precision, const FimLaunch& a, int grid_fields, cudaStream_t st);
@@ -97,9 +97,9 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
-                           const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
+                           const uint32_t* region_map, const void* regions64, int nregions, const uint8_t* records,
                            const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
-                           cudaStream_t st, int vtable = 0);
+                           cudaStream_t st, int vtable = 0, double* F_out = nullptr, uint8_t* rec_out = nullptr);
 cudaError_t launch_eval_velocity(const MatD* mat, int kind, int group_model, int precision, const double* angles,
                                  double* out, int n, cudaStream_t st);
 
@@ -108,8 +108,8 @@ struct HierLaunch {
     void* times;
     const FieldDesc* fields;
     int nfields;
-    const uint16_t* region_map;
-    const uint16_t* region_mat;
+    const uint32_t* region_map;
+    const uint32_t* region_mat;
     const MatD* mats;
     const void* regions;  // RegionP<T>
     const double* theta;
@@ -140,8 +140,8 @@ struct AdjLaunch {
     const FieldDesc* fields;
     int nfields, nsamples, nrec;
     size_t total_nodes;
-    const uint16_t* region_map;
-    const uint16_t* region_mat;
+    const uint32_t* region_map;
+    const uint32_t* region_mat;
     const MatD* mats;
     const void* regions;  // RegionP<T>
     const double* theta;
@@ -173,8 +173,8 @@ struct RayLaunch {
     const void* times;
     const FieldDesc* fields;
     int nfields;
-    const uint16_t* region_map;
-    const uint16_t* region_mat;
+    const uint32_t* region_map;
+    const uint32_t* region_mat;
     const MatD* mats;
     const void* regions;  // RegionP<T>
     const double* theta;
@@ -209,7 +209,8 @@ struct alf_ctx {
 
 struct alf_plan {
     alf_ctx* ctx = nullptr;
-    alf_options opt{};
+    alf_options opt{};         // in effect: lengths in cells of the (sub-grid refined) plan grid
+    alf_options opt_caller{};  // as given, lengths in original cells
     int B = 0, S = 0, Rr = 0, R = 0, nmat = 0, nfields = 0;
     std::vector<alf::FieldDesc> fields;
     std::vector<size_t> field_off;
@@ -222,8 +223,8 @@ struct alf_plan {
     int box = 0;  // half-width of the frozen box around each source
     // device
     alf::FieldDesc* d_fields = nullptr;
-    uint16_t* d_map = nullptr;
-    uint16_t* d_region_mat = nullptr;
+    uint32_t* d_map = nullptr;  // region id of every node, samples back to back
+    uint32_t* d_region_mat = nullptr;
     alf::MatD* d_mats = nullptr;
     double* d_h = nullptr;
     int32_t* d_rec = nullptr;

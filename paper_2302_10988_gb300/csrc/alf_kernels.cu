@@ -35,7 +35,7 @@ ALF_D void set_error(QueueState* q, unsigned code) { atomicCAS(&q->error, 0u, co
 // prep_regions
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void prep_regions_kernel(const MatD* mats, const uint16_t* region_mat, const double* theta, const double* h,
+__global__ void prep_regions_kernel(const MatD* mats, const uint32_t* region_mat, const double* theta, const double* h,
                                     int nsamples, int nregions, int group_model, RegionP<T>* out, const T* vtab)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,7 +69,7 @@ __global__ void prep_regions_kernel(const MatD* mats, const uint16_t* region_mat
     out[k] = R;
 }
 
-cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint16_t* region_mat, const double* theta,
+cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint32_t* region_mat, const double* theta,
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
                                 cudaStream_t st, const void* vtab)
 {
@@ -145,8 +145,8 @@ cudaError_t launch_set_status(QueueState* q, unsigned code, cudaStream_t st)
 // init_radius: one block per field; frozen nodes store -tau (sign bit = frozen)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void init_radius_kernel(T* times, const FieldDesc* fields, const uint16_t* region_map,
-                                   const uint16_t* region_mat, const MatD* mats, const double* theta, const double* h,
+__global__ void init_radius_kernel(T* times, const FieldDesc* fields, const uint32_t* region_map,
+                                   const uint32_t* region_mat, const MatD* mats, const double* theta, const double* h,
                                    int nregions, int r0, int group_model, unsigned* frozen_bits, int box)
 {
     const FieldDesc fd = fields[blockIdx.x];
@@ -172,7 +172,7 @@ __global__ void init_radius_kernel(T* times, const FieldDesc* fields, const uint
 }
 
 cudaError_t launch_init_radius(int precision, void* times, const FieldDesc* fields, int nfields,
-                               const uint16_t* region_map, const uint16_t* region_mat, const MatD* mats,
+                               const uint32_t* region_map, const uint32_t* region_mat, const MatD* mats,
                                const double* theta, const double* h, int nregions, int r0, int group_model,
                                unsigned* frozen_bits, int box, cudaStream_t st)
 {
@@ -892,9 +892,10 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
 }
 
 template <typename T, bool VT>
-__global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint16_t* region_map,
+__global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint32_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
-                               const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips)
+                               const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips,
+                               double* F_out, uint8_t* rec_out)
 {
     // persistent: the CTAs stride over (field, chunk) work items, so that a small grid leaves room on
     // the SMs for kernels of other streams while this one keeps the FP64 pipe busy
@@ -912,9 +913,14 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
     const T* tf = times + fd.node_off;
     for (int me = chunk * blockDim.x + threadIdx.x; me < n; me += CH * blockDim.x) {
         const int i = me % fd.nx, j = me / fd.nx;
-        if (box_frozen(fb, box, fd, i, j)) continue;
         const T tme = abs_(tf[me]);
-        if (!(tme < alf_inf<T>())) continue;
+        // frozen nodes and nodes without a value keep their time (records 254 / 255)
+        const bool fz = box_frozen(fb, box, fd, i, j);
+        if (fz || !(tme < alf_inf<T>())) {
+            if (F_out) F_out[fd.node_off + me] = (double)tme;
+            if (rec_out) rec_out[fd.node_off + me] = fz ? 254 : 255;
+            continue;
+        }
         T t[12];
         unsigned known = 0u;
 #pragma unroll
@@ -1017,6 +1023,8 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
         const float res = fabsf((float)(F - (double)tme)) / (float)tme;
         if (tme > T(0)) mx = fmaxf(mx, res);
         if (records && records[fd.node_off + me] != (uint8_t)rec) flips++;
+        if (F_out) F_out[fd.node_off + me] = F;
+        if (rec_out) rec_out[fd.node_off + me] = (uint8_t)rec;
     }
     s_max[threadIdx.x] = mx;
     s_flip[threadIdx.x] = flips;
@@ -1039,9 +1047,9 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
 }
 
 cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fields, int nfields,
-                           const uint16_t* region_map, const void* regions64, int nregions, const uint8_t* records,
+                           const uint32_t* region_map, const void* regions64, int nregions, const uint8_t* records,
                            const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips, int grid_ctas,
-                           cudaStream_t st, int vtable)
+                           cudaStream_t st, int vtable, double* F_out, uint8_t* rec_out)
 {
     cudaError_t e = cudaMemsetAsync(max_rel, 0, sizeof(double) * nfields, st);
     if (e != cudaSuccess) return e;
@@ -1052,17 +1060,21 @@ cudaError_t launch_check64(int precision, const void* times, const FieldDesc* fi
     if (precision == ALF_FP64) {
         if (vtable)
             check64_kernel<double, true><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map, R64,
-                                                               nregions, records, frozen_bits, box, max_rel, n_flips);
+                                                               nregions, records, frozen_bits, box, max_rel, n_flips, F_out,
+                                                               rec_out);
         else
             check64_kernel<double, false><<<grid, 256, 0, st>>>((const double*)times, fields, nfields, region_map, R64,
-                                                                nregions, records, frozen_bits, box, max_rel, n_flips);
+                                                                nregions, records, frozen_bits, box, max_rel, n_flips, F_out,
+                                                               rec_out);
     } else {
         if (vtable)
             check64_kernel<float, true><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map, R64,
-                                                              nregions, records, frozen_bits, box, max_rel, n_flips);
+                                                              nregions, records, frozen_bits, box, max_rel, n_flips, F_out,
+                                                               rec_out);
         else
             check64_kernel<float, false><<<grid, 256, 0, st>>>((const float*)times, fields, nfields, region_map, R64,
-                                                               nregions, records, frozen_bits, box, max_rel, n_flips);
+                                                               nregions, records, frozen_bits, box, max_rel, n_flips, F_out,
+                                                               rec_out);
     }
     note_launches(1);
     return cudaGetLastError();

@@ -29,7 +29,7 @@
 namespace alf {
 namespace {
 
-// Limits of the allocation-free solve (the array is about 7 MB).
+// Limits of the allocation-free solve (the array is about 8 MB).
 constexpr int kNoAllocMaxNodes = 512 * 512;
 constexpr int kNoAllocMaxRegions = 1024;
 constexpr int kNoAllocMaxMaterials = 64;
@@ -54,7 +54,9 @@ constexpr size_t kOffEfield = align256(kOffElist + sizeof(unsigned) * kNoAllocMa
 constexpr size_t kOffOld = align256(kOffEfield + sizeof(unsigned) * kNoAllocMaxNodes);
 constexpr size_t kOffNew = align256(kOffOld + sizeof(float) * kNoAllocMaxNodes);
 constexpr size_t kOffBitmap = align256(kOffNew + sizeof(float) * kNoAllocMaxNodes);
-constexpr size_t kScratchBytes = align256(kOffBitmap + sizeof(unsigned) * ((kNoAllocMaxNodes + 31) / 32));
+constexpr size_t kOffMap32 = align256(kOffBitmap + sizeof(unsigned) * ((kNoAllocMaxNodes + 31) / 32));
+constexpr size_t kOffRmat32 = align256(kOffMap32 + sizeof(uint32_t) * kNoAllocMaxNodes);
+constexpr size_t kScratchBytes = align256(kOffRmat32 + sizeof(uint32_t) * kNoAllocMaxRegions);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -79,16 +81,23 @@ cudaError_t scratch_address(unsigned char** out)
     return cudaSuccess;
 }
 
-// Flags (word *bad = 1) a region id >= nregions in the map or a material id >= nmaterials in the region
-// table: the kernels index the region constants and the material table with them.
+// Copies the caller's 16-bit region map and region->material table into the 32-bit ones the kernels read, and
+// flags (word *bad = 1) a region id >= nregions or a material id >= nmaterials: the kernels index the region
+// constants and the material table with them.
 __global__ void check_ids_kernel(const uint16_t* region_map, int n, const uint16_t* region_material, int nregions,
-                                 int nmaterials, unsigned* bad)
+                                 int nmaterials, uint32_t* map32, uint32_t* rmat32, unsigned* bad)
 {
     bool out = false;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-        out |= region_map[k] >= nregions;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nregions; k += gridDim.x * blockDim.x)
-        out |= region_material[k] >= nmaterials;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t r = region_map[k];
+        map32[k] = r;
+        out |= r >= (uint32_t)nregions;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nregions; k += gridDim.x * blockDim.x) {
+        const uint32_t m = region_material[k];
+        rmat32[k] = m;
+        out |= m >= (uint32_t)nmaterials;
+    }
     if (out) *bad = 1u;
 }
 
@@ -198,6 +207,7 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
     if (e == cudaSuccess) {
         const int blocks = std::max(1, std::min(device_sm_count() * 4, (int)((N + 255) / 256)));
         check_ids_kernel<<<blocks, 256, 0, st>>>(region_map, (int)N, region_material, nregions, nmaterials,
+                                                 (uint32_t*)(S + kOffMap32), (uint32_t*)(S + kOffRmat32),
                                                  (unsigned*)(S + kOffCounters + 96));
         note_launches(1);
         e = cudaGetLastError();
@@ -209,23 +219,25 @@ extern "C" alf_status alf_solve_field_noalloc(int cuda_device, const alf_materia
         return nfail(err, err_len, ALF_ERR_INVALID_ARG,
                      "alf_solve_field_noalloc: a region id >= nregions or a material id >= nmaterials");
     const FieldDesc* d_fd = (const FieldDesc*)(S + kOffField);
+    const uint32_t* d_map32 = (const uint32_t*)(S + kOffMap32);
+    const uint32_t* d_rmat32 = (const uint32_t*)(S + kOffRmat32);
     const MatD* d_mats = (const MatD*)(S + kOffMats);
     const double* d_h = (const double*)(S + kOffH);
     unsigned* d_frozen = (unsigned*)(S + kOffFrozen);
     QueueState* d_q = (QueueState*)(S + kOffQ);
     unsigned* ctr = (unsigned*)(S + kOffCounters);
     if (e == cudaSuccess)
-        e = launch_prep_regions(ALF_FP32, d_mats, region_material, region_theta, d_h, 1, nregions, group_model,
+        e = launch_prep_regions(ALF_FP32, d_mats, d_rmat32, region_theta, d_h, 1, nregions, group_model,
                                 S + kOffRegions, st);
     if (e == cudaSuccess) e = launch_fill_inf(ALF_FP32, times, N, st);
     if (e == cudaSuccess)
-        e = launch_init_radius(ALF_FP32, times, d_fd, 1, region_map, region_material, d_mats, region_theta, d_h,
+        e = launch_init_radius(ALF_FP32, times, d_fd, 1, d_map32, d_rmat32, d_mats, region_theta, d_h,
                                nregions, init_radius, group_model, d_frozen, init_radius, st);
     FimLaunch a{};
     a.times = times;
     a.fields = d_fd;
     a.nfields = 1;
-    a.region_map = region_map;
+    a.region_map = d_map32;
     a.regions = S + kOffRegions;
     a.nregions = nregions;
     a.box = init_radius;

@@ -41,8 +41,8 @@ template <typename T>
 struct RayCtx {
     int nx, ny;
     long long map_off;
-    const uint16_t* map;
-    const uint16_t* region_mat;
+    const uint32_t* map;
+    const uint32_t* region_mat;
     const MatD* mats;
     const RegionP<T>* regions;  // of this sample
     const double* theta;        // of this sample
@@ -338,7 +338,7 @@ __global__ void ray_grad_kernel(RayLaunch a, const T* dL_dray, double* grad)
     const int b = fd.sample;
     const double h = a.h_of_sample[b];
     const double* theta = a.theta + (size_t)b * a.nregions;
-    const uint16_t* map = a.region_map + fd.map_off;
+    const uint32_t* map = a.region_map + fd.map_off;
     double* gb = grad + (size_t)b * a.nregions;
     const T* pts = (const T*)a.pts + (size_t)ray * a.max_pts * 2;
     int cur = -1;

@@ -27,7 +27,7 @@ template <typename T>
 struct WarpGrid {
     T* tf;                      // times of the grid (frozen nodes carry the sign bit)
     int nx, ny;
-    const uint16_t* map;        // region id of every node
+    const uint32_t* map;        // region id of every node
     const RegionP<T>* reg;      // region constants of the sample
     T scale;                    // spacing of this grid / spacing of the regions' grid
     unsigned* list0;            // dirty lists and evaluation list, nx * ny entries each

@@ -74,3 +74,84 @@ def test_adjoint_schedules_agree(api):
         out.append(P.backward(th, times, rec, 2.0 * rt))
         assert P.status() == 0
     assert torch.allclose(out[0], out[1], rtol=0, atol=1e-9 * out[0].abs().max().item())
+
+
+def _inside_sources(nsamples=2):
+    """3 x 3 weld grains on 40 x 40 with the sources inside grains (the frozen nodes around each source then
+    depend on the orientation of its grain), receivers on the top edge."""
+    wl, truth = W.weld_adjoint(nsamples=nsamples, n=40, rg=3, nsrc=2, nrec=6)
+    for s in wl.samples + truth.samples:
+        s.src[:] = [[20, 20], [12, 28]]
+    return wl, truth
+
+
+def _elementwise(g, g_o, floor=1e-2):
+    """Largest relative error over the components that are not tiny (|g_o| >= floor * max |g_o|)."""
+    m = np.abs(g_o) >= floor * np.abs(g_o).max()
+    return float((np.abs(g - g_o)[m] / np.abs(g_o)[m]).max()), int(m.sum())
+
+
+@pytest.mark.parametrize("r0", [2, 0])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 2e-3)])
+def test_backward_source_grain_and_fallback(api, oracle, precision, tol, r0):
+    """The frozen-node branch (sources inside grains, r0 = 2) and the fallback branch (no frozen box, r0 = 0:
+    the nodes next to each source have no usable stencil) against the oracle's adjoint, element by element."""
+    wl, truth = _inside_sources()
+    _, _, t_true = oracle.misfit_and_gradient(truth, 0, truth.samples[0].region_theta, np.zeros((2, 6)), r0=r0)
+    t_obs = t_true + W.observation_noise(t_true.shape)
+    P = api.Plan(wl, precision=precision, keep_records=1, init_radius=r0)
+    th = P.theta_tensor()
+    rec = P.new_records()
+    times, rt = P.solve(th, records=rec)
+    g = P.backward(th, times, rec, 2.0 * (rt.double() - torch.as_tensor(t_obs, device=rt.device)[None]))
+    assert P.status() == 0
+    g = g.cpu().numpy()
+    rm = wl.samples[0].region_map
+    src_regions = sorted({int(rm[sj, si]) for si, sj in wl.samples[0].src})
+    for b in range(len(wl.samples)):
+        _, g_o, _ = oracle.misfit_and_gradient(wl, b, wl.samples[b].region_theta, t_obs, r0=r0)
+        err, n = _elementwise(g[b], g_o)
+        print(f"{precision} r0={r0} sample {b}: element-wise rel error {err:.2e} over {n} components; "
+              f"source grains {[(r, g[b][r], g_o[r]) for r in src_regions]}")
+        assert err < tol
+        assert all(abs(g_o[r]) > 0 for r in src_regions)
+
+
+def test_backward_central_differences_fp64(api):
+    """The GPU gradient against central differences of the GPU's own FP64 forward map (step 1e-4 rad), every
+    sample and grain at once; components whose stencil records change inside the step are left out."""
+    wl, truth = W.weld_adjoint(nsamples=4, n=80, rg=4, nsrc=4, nrec=8)
+    P = api.Plan(wl, precision="fp64", keep_records=1)
+    th = P.theta_tensor()
+    tob = torch.zeros((4, 4, 8), dtype=torch.float64, device=th.device)
+    rec = P.new_records()
+    times, rt = P.solve(th, records=rec)
+    g = P.backward(th, times, rec, 2.0 * (rt - tob)).cpu().numpy()
+    assert P.status() == 0
+    e = 1e-4
+    checked = skipped = 0
+    worst = 0.0
+    S = P.nsrc
+    for r in range(1, P.nregions):
+        Ls, recs = [], []
+        for sgn in (1.0, -1.0):
+            thp = th.clone()
+            thp[:, r] += sgn * e
+            rp = P.new_records()
+            _, rtp = P.solve(thp, records=rp)
+            Ls.append(((rtp - tob) ** 2).sum(dim=(1, 2)).cpu().numpy())
+            recs.append(rp)
+        assert P.status() == 0
+        fd = (Ls[0] - Ls[1]) / (2 * e)
+        for b in range(4):
+            lo, hi = P.offsets[b * S], P.offsets[(b + 1) * S]
+            if not torch.equal(recs[0][lo:hi], recs[1][lo:hi]):
+                skipped += 1
+                continue
+            err = abs(g[b, r] - fd[b]) / max(abs(fd[b]), 1e-30)
+            worst = max(worst, err)
+            assert abs(g[b, r] - fd[b]) <= 1e-4 * abs(fd[b]) + 1e-20, (b, r, g[b, r], fd[b])
+            checked += 1
+    print(f"GPU FP64 gradient vs central differences: {checked} components checked (worst {worst:.2e}), "
+          f"{skipped} left out for record flips")
+    assert checked >= 20

@@ -115,7 +115,8 @@ def test_weld_256_fp64_and_fp32(api, oracle):
     mr, fl = P32.check64(th, t32, rec32)
     torch.cuda.synchronize()
     print(f"FP64 check of FP32 fields: max residual {mr.max().item():.3e}, flips {int(fl.sum())}")
-    assert mr.max().item() < 1e-4
+    # an FP32 field sits at the FP64 fixed point to FP32 rounding (a few ulp of the stencil arithmetic)
+    assert mr.max().item() < 1e-6
     mr64, fl64 = P64.check64(th, t64, rec64)
     torch.cuda.synchronize()
     assert mr64.max().item() < 1e-12 and int(fl64.sum()) == 0

@@ -1,0 +1,101 @@
+"""Per-node orientation and stiffness maps (Sec. 3.2: every node may carry its own orthotropic stiffness and
+orientation): a region per node, so region ids and material ids go beyond 16 bits, against the oracle, which
+takes per-node materials and orientations directly; and a per-node orientation map at the size of the large
+single medium (2048 x 2048, 4.2 million regions)."""
+import numpy as np
+import pytest
+
+from paper_2302_10988_gb300 import workloads as W
+from tests.gpu_helpers import record_mismatch, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2302_10988_gb300 import build
+    build.build()
+    from paper_2302_10988_gb300 import api as A
+    return A
+
+
+def smooth_orientation(nx, ny, seed):
+    """A grain-orientation field that varies from node to node: smooth bands plus per-node scatter."""
+    rng = np.random.default_rng(seed)
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    th = 0.6 * np.sin(ii / 37.0 + 0.3) + 0.5 * np.cos(jj / 29.0) + rng.normal(0.0, 0.05, (ny, nx))
+    return th.ravel()
+
+
+def per_node_workload(nx, ny, h, src, rec, theta, stiffness=None):
+    """Region k = node k; materials: the weld's TI stiffness for every node, or one material per node."""
+    n = nx * ny
+    rm = np.arange(n, dtype=np.uint32).reshape(ny, nx)
+    if stiffness is None:
+        mats, rmat = [W.WELD_TI], np.zeros(n, np.uint32)
+    else:
+        mats, rmat = stiffness, np.arange(n, dtype=np.uint32)
+    s = W.Sample(nx, ny, h, rm, np.asarray(theta, np.float64), np.asarray(src, np.int32), np.asarray(rec, np.int32))
+    return W.Workload(f"per-node {nx}x{ny}", mats, rmat, [s])
+
+
+def test_per_node_orientation_and_stiffness(api, oracle):
+    """300 x 260 nodes, each with its own orientation and its own TI stiffness (C11 and C33 varying by up to
+    +-8 % across the grid): 78,000 regions and materials, beyond 16-bit ids."""
+    nx, ny, h = 300, 260, 0.5e-3
+    n = nx * ny
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    f = (0.08 * np.sin(ii / 50.0) * np.cos(jj / 40.0)).ravel()
+    G = W.GPA
+    stiff = [(W.ti_voigt(234 * G * (1 + f[k]), 216 * G * (1 - f[k]), 145 * G, 129 * G), 8100.0) for k in range(n)]
+    theta = smooth_orientation(nx, ny, 5)
+    wl = per_node_workload(nx, ny, h, [[10, 0], [150, 130]], [[290, 259], [0, 259]], theta, stiff)
+    mats = [oracle.mat_from_voigt(c6, rho) for c6, rho in stiff]
+    M = oracle.OMedium(nx, ny, h, np.arange(n, dtype=np.int32), theta, mats)
+    for precision, tol in (("fp64", 1e-6), ("fp32", 1e-4)):
+        P = api.Plan(wl, precision=precision)
+        th = P.theta_tensor()
+        rec = P.new_records()
+        times, rt = P.solve(th, records=rec)
+        assert P.status() == 0
+        flips = 0
+        for k, (si, sj) in enumerate(wl.samples[0].src):
+            fr, t0 = oracle.init_radius(M, int(si), int(sj), 2)
+            tau, orec, st = oracle.fmm(M, fr, t0)
+            e = rel_err(P.field(times, k).cpu().numpy(), tau).max()
+            flips += record_mismatch(P.field(rec, k).cpu().numpy(), orec, fr.reshape(ny, nx))
+            print(f"per-node {precision} source {k}: max rel {e:.2e}")
+            assert e < tol
+        if precision == "fp64":
+            assert flips == 0
+
+
+def test_per_node_orientation_2048(api, oracle):
+    """2048 x 2048 at 0.1 mm with a per-node orientation map (4,194,304 regions), 8 sources on the bottom edge
+    and 256 receivers on the top: the FP64 check of every node, all rays complete, one field against the
+    oracle."""
+    n = 2048
+    theta = smooth_orientation(n, n, 11)
+    src = W.edge_nodes(n, 8, 0)
+    rec = W.edge_nodes(n, 256, n - 1)
+    wl = per_node_workload(n, n, 0.1e-3, src, rec, theta)
+    P = api.Plan(wl, precision="fp32", max_ray_points=1024)
+    th = P.theta_tensor()
+    rec_t = P.new_records()
+    times, rt = P.solve(th, records=rec_t)
+    mr, fl = P.check64(th, times, rec_t)
+    pts, npts, rtime, rst = P.trace_rays(th, times)
+    assert P.status() == 0
+    print(f"per-node 2048: FP64 check max residual {mr.max().item():.2e}, flips {int(fl.sum())}")
+    assert mr.max().item() < 1e-6
+    assert (rst == 0).all()
+    ratio = (rtime / rt).cpu().numpy()
+    assert 0.98 < ratio.min() and ratio.max() < 1.02
+    mats = [oracle.mat_from_voigt(*W.WELD_TI)]
+    M = oracle.OMedium(n, n, 0.1e-3, np.zeros(n * n, np.int32), theta, mats)
+    fr, t0 = oracle.init_radius(M, int(src[3][0]), int(src[3][1]), 2)
+    tau = oracle.fmm(M, fr, t0)[0]
+    e = rel_err(P.field(times, 3).cpu().numpy(), tau)
+    print(f"per-node 2048 source 3 vs oracle: max rel {e.max():.2e}, mean {e.mean():.2e}")
+    assert e.max() < 1e-4
