@@ -34,6 +34,7 @@
  * (Sec. 3.2): only c22, c23, c33, c44 and the density enter the qP speed. */
 typedef struct {
     double c22, c23, c33, c44, rho;
+    double c55, c66; /* the out-of-plane shear constants: only the SH mode reads them */
 } om_mat;
 
 /* A medium on a regular grid: per-node material index and orientation.
@@ -49,6 +50,8 @@ typedef struct {
     int group_model; /* 0 = the paper's group->phase inversion, 1 = exact ray velocity */
     int vtable;      /* 1: stencil updates take the phase speed by linear interpolation in a table of phase
                         speeds at integer degrees (Sec. 3, Sec. 4.2); 0: from the Christoffel matrix */
+    int wave_mode;   /* 0: qP; 1: qSV; 2: SH (Sec. 7: the other eigenvalues of Sec. 3.2) */
+    const double* env; /* wave modes 1, 2: per material, ENV_N first-arrival slownesses (see below) */
 } om_medium;
 
 /* counters exposed for tests */
@@ -93,6 +96,78 @@ double om_qp_lambda(const om_mat* m, double theta)
 double om_phase_velocity(const om_mat* m, double theta)
 {
     return sqrt(om_qp_lambda(m, theta) / m->rho);
+}
+
+/* Sec. 3.2 and Sec. 7: the eigenvalue of the Christoffel matrix of each wave mode at phase angle theta.
+ * mode 0 (qP): the larger root of the in-plane 2x2 block; mode 1 (qSV): the smaller root,
+ * ((alpha + gamma) - sqrt((alpha - gamma)^2 + 4 beta^2)) / 2; mode 2 (SH): the out-of-plane eigenvalue
+ * cos^2(theta) c66 + sin^2(theta) c55 (eigenvector (1, 0, 0)). */
+double om_mode_lambda(const om_mat* m, int mode, double theta)
+{
+    double c = cos(theta), s = sin(theta);
+    if (mode == 2) return c * c * m->c66 + s * s * m->c55;
+    if (mode == 0) return om_qp_lambda(m, theta);
+    double alpha = c * c * m->c22 + s * s * m->c44;
+    double beta = c * s * (m->c23 + m->c44);
+    double gamma = c * c * m->c44 + s * s * m->c33;
+    return 0.5 * ((alpha + gamma) - sqrt((alpha - gamma) * (alpha - gamma) + 4.0 * beta * beta));
+}
+
+double om_mode_velocity(const om_mat* m, int mode, double theta)
+{
+    return sqrt(om_mode_lambda(m, mode, theta) / m->rho);
+}
+
+/* First-arrival group slowness of a mode along the angle psi from the material axis: the support function
+ * of the slowness curve, max over phase angles theta of cos(theta - psi) / v(theta) (the wavefront of a point
+ * source in a homogeneous medium is the envelope of the plane waves n.x = v(n) t, so the first arrival at
+ * distance d along psi is d times this maximum).  It is single valued where the qSV ray surface has cusps.
+ * Evaluated by a scan of 3600 phase angles over (psi - 90, psi + 90] degrees and a golden-section search
+ * around the best one. */
+double om_envelope_slowness(const om_mat* m, int mode, double psi)
+{
+    const int n = 3600;
+    const double step = M_PI / n;
+    double best = -1.0, bt = psi;
+    for (int k = 1; k <= n; ++k) {
+        double th = psi - M_PI / 2 + k * step;
+        double g = cos(th - psi) / om_mode_velocity(m, mode, th);
+        if (g > best) {
+            best = g;
+            bt = th;
+        }
+    }
+    double a = bt - step, b = bt + step;
+    const double r = 0.5 * (sqrt(5.0) - 1.0);
+    for (int it = 0; it < 80; ++it) {
+        double x1 = b - r * (b - a), x2 = a + r * (b - a);
+        double g1 = cos(x1 - psi) / om_mode_velocity(m, mode, x1);
+        double g2 = cos(x2 - psi) / om_mode_velocity(m, mode, x2);
+        if (g1 < g2) a = x1; else b = x2;
+    }
+    double th = 0.5 * (a + b);
+    double g = cos(th - psi) / om_mode_velocity(m, mode, th);
+    return g > best ? g : best;
+}
+
+/* [R20] The group speeds of the shear modes (source initialisation, fallback, rays) come from a table of the
+ * envelope slowness at ENV_N angles 0, 1/8, ..., 180 degrees from the material axis, interpolated linearly in
+ * slowness (the paper tabulates velocity curves in the same way, Sec. 3). */
+#define ENV_N 1441
+void om_envelope_table(const om_mat* m, int mode, double* tab)
+{
+    for (int k = 0; k < ENV_N; ++k) tab[k] = om_envelope_slowness(m, mode, k * M_PI / (ENV_N - 1));
+}
+
+static double envelope_speed(const double* tab, double psi)
+{
+    double deg = psi * 180.0 / M_PI;
+    deg -= 180.0 * floor(deg / 180.0); /* [0, 180) */
+    double u = deg * (ENV_N - 1) / 180.0;
+    int k = (int)floor(u);
+    if (k > ENV_N - 2) k = ENV_N - 2;
+    double f = u - k;
+    return 1.0 / ((1.0 - f) * tab[k] + f * tab[k + 1]);
 }
 
 /* Sec. 3.2, Eq. lambda_1: lambda from the phase angle theta and group angle phi. */
@@ -227,6 +302,13 @@ double om_group_speed(const om_mat* m, int model, double dir, double theta_mat)
     return V;
 }
 
+/* The medium's group speed of material `mat` along dir: the qP models above, or the shear modes' table. */
+static double med_group_speed(const om_medium* M, int mat, double dir, double theta_mat)
+{
+    if (M->wave_mode != 0) return envelope_speed(M->env + (size_t)mat * ENV_N, dir - theta_mat);
+    return om_group_speed(&M->mats[mat], M->group_model, dir, theta_mat);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 4.1: the 32 stencils, written as printed (Tables square_sten and      */
 /* triangle_sten), offsets (di, dj) of A, B, C relative to D = (i, j).         */
@@ -306,10 +388,11 @@ static double stencil_time(const om_medium* M, int d, const double xa[3], const 
         if (k > 179) k = 179;
         double f = deg - k;
         const om_mat* m = &M->mats[M->mat_id[d]];
-        double v0 = om_phase_velocity(m, k * M_PI / 180.0), v1 = om_phase_velocity(m, (k + 1) * M_PI / 180.0);
+        double v0 = om_mode_velocity(m, M->wave_mode, k * M_PI / 180.0);
+        double v1 = om_mode_velocity(m, M->wave_mode, (k + 1) * M_PI / 180.0);
         v = (1.0 - f) * v0 + f * v1;
     } else {
-        v = om_phase_velocity(&M->mats[M->mat_id[d]], theta_p);
+        v = om_mode_velocity(&M->mats[M->mat_id[d]], M->wave_mode, theta_p);
     }
     return tB + FD * M->h / v;
 }
@@ -391,14 +474,13 @@ static double update_from_set(const om_medium* M, int i, int j, const int known[
         return best_val;
     }
     /* [R8] fallback */
-    const om_mat* m = &M->mats[M->mat_id[d]];
     double best = OM_INF;
     int bk = -1;
     for (int k = 0; k < 12; ++k) {
         if (!known[k]) continue;
         double di = -DIAMOND[k][0], dj = -DIAMOND[k][1]; /* direction N -> D */
         double len = sqrt(di * di + dj * dj);
-        double V = om_group_speed(m, M->group_model, atan2(dj, di), M->theta[d]);
+        double V = med_group_speed(M, M->mat_id[d], atan2(dj, di), M->theta[d]);
         double val = t[k] + len * M->h / V;
         g_ops += 2;
         if (val < best) {
@@ -740,7 +822,6 @@ void om_init_radius(const om_medium* M, int si, int sj, int r0, uint8_t* frozen,
 {
     int nx = M->nx;
     int s = sj * nx + si;
-    const om_mat* m = &M->mats[M->mat_id[s]];
     for (int n = 0; n < nx * M->ny; ++n) {
         frozen[n] = 0;
         tau[n] = OM_INF;
@@ -756,7 +837,7 @@ void om_init_radius(const om_medium* M, int si, int sj, int r0, uint8_t* frozen,
                 continue;
             }
             double dist = sqrt((double)(di * di + dj * dj)) * M->h;
-            tau[n] = dist / om_group_speed(m, M->group_model, atan2((double)dj, (double)di), M->theta[s]);
+            tau[n] = dist / med_group_speed(M, M->mat_id[s], atan2((double)dj, (double)di), M->theta[s]);
         }
 }
 
@@ -797,7 +878,7 @@ static double seg_time(const om_medium* M, double x0, double y0, double x1, doub
     if (mi >= M->nx) mi = M->nx - 1;
     if (mj >= M->ny) mj = M->ny - 1;
     int n = mj * M->nx + mi;
-    double V = om_group_speed(&M->mats[M->mat_id[n]], M->group_model, atan2(dy, dx), M->theta[n]);
+    double V = med_group_speed(M, M->mat_id[n], atan2(dy, dx), M->theta[n]);
     return len * M->h / V;
 }
 
@@ -981,7 +1062,7 @@ double om_path_time(const om_medium* M, const double* pts, int npts)
             if (mi >= M->nx) mi = M->nx - 1;
             if (mj >= M->ny) mj = M->ny - 1;
             int n = mj * M->nx + mi;
-            double V = om_group_speed(&M->mats[M->mat_id[n]], M->group_model, dir, M->theta[n]);
+            double V = med_group_speed(M, M->mat_id[n], dir, M->theta[n]);
             total += (tb - ta) * len * M->h / V;
         }
     }
@@ -1005,7 +1086,6 @@ int om_init_hierarchy(const om_medium* M, int si, int sj, int nlev, const int* d
                       uint8_t* frozen_out, double* tau_out)
 {
     int nx = M->nx, ny = M->ny;
-    const om_mat* msrc = &M->mats[M->mat_id[sj * nx + si]];
     double th_src = M->theta[sj * nx + si];
     /* previous level's known set, on its own grid */
     uint8_t* pk = NULL;
@@ -1046,7 +1126,8 @@ int om_init_hierarchy(const om_medium* M, int si, int sj, int nlev, const int* d
                         double dist = sqrt((double)a * a + (double)b * b) * M->h / d;
                         tau[n] = (a == 0 && b == 0)
                                      ? 0.0
-                                     : dist / om_group_speed(msrc, M->group_model, atan2((double)b, (double)a), th_src);
+                                     : dist / med_group_speed(M, M->mat_id[sj * nx + si], atan2((double)b, (double)a),
+                                                              th_src);
                     }
                 } else {
                     /* coincides with a node of the previous level? */
@@ -1155,10 +1236,9 @@ void om_adjoint(const om_medium* M, const uint8_t* frozen, const double* tau, co
             int nN = (j + DIAMOND[k2][1]) * nx + i + DIAMOND[k2][0];
             double di = -DIAMOND[k2][0], dj = -DIAMOND[k2][1];
             double len = sqrt(di * di + dj * dj);
-            const om_mat* m = &M->mats[M->mat_id[d]];
             double dir = atan2(dj, di);
-            double Vp = om_group_speed(m, M->group_model, dir, th0 + 1e-6);
-            double Vm = om_group_speed(m, M->group_model, dir, th0 - 1e-6);
+            double Vp = med_group_speed(M, M->mat_id[d], dir, th0 + 1e-6);
+            double Vm = med_group_speed(M, M->mat_id[d], dir, th0 - 1e-6);
             double dT = (len * M->h / Vp - len * M->h / Vm) / 2e-6;
             lam[nN] += lam[d];
             grad[region[d]] += lam[d] * dT;
@@ -1166,15 +1246,14 @@ void om_adjoint(const om_medium* M, const uint8_t* frozen, const double* tau, co
     }
     /* frozen nodes: straight-ray times from the source, orientation of the source */
     int s = sj * nx + si;
-    const om_mat* ms = &M->mats[M->mat_id[s]];
     for (int n = 0; n < N; ++n) {
         if (!frozen[n] || n == s || lam[n] == 0.0) continue;
         double di = n % nx - si, dj = n / nx - sj;
         double dist = sqrt(di * di + dj * dj) * M->h;
         double dir = atan2(dj, di);
         double th = M->theta[s];
-        double dT = (dist / om_group_speed(ms, M->group_model, dir, th + 1e-6)
-                     - dist / om_group_speed(ms, M->group_model, dir, th - 1e-6)) / 2e-6;
+        double dT = (dist / med_group_speed(M, M->mat_id[s], dir, th + 1e-6)
+                     - dist / med_group_speed(M, M->mat_id[s], dir, th - 1e-6)) / 2e-6;
         grad[region[s]] += lam[n] * dT;
     }
     free(lam);

@@ -38,13 +38,18 @@ def build(force: bool = False) -> str:
 
 class Mat(C.Structure):
     _fields_ = [("c22", C.c_double), ("c23", C.c_double), ("c33", C.c_double), ("c44", C.c_double),
-                ("rho", C.c_double)]
+                ("rho", C.c_double), ("c55", C.c_double), ("c66", C.c_double)]
 
 
 class Medium(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double),
                 ("mat_id", C.POINTER(C.c_int32)), ("theta", C.POINTER(C.c_double)),
-                ("mats", C.POINTER(Mat)), ("nmats", C.c_int), ("group_model", C.c_int), ("vtable", C.c_int)]
+                ("mats", C.POINTER(Mat)), ("nmats", C.c_int), ("group_model", C.c_int), ("vtable", C.c_int),
+                ("wave_mode", C.c_int), ("env", C.POINTER(C.c_double))]
+
+
+QP, QSV, SH = 0, 1, 2
+ENV_N = 1441  # envelope table entries: 0, 1/8, ..., 180 degrees
 
 
 class RayOpts(C.Structure):
@@ -62,6 +67,14 @@ def lib():
             L.om_qp_lambda.argtypes = [P(Mat), C.c_double]
             L.om_phase_velocity.restype = C.c_double
             L.om_phase_velocity.argtypes = [P(Mat), C.c_double]
+            L.om_mode_lambda.restype = C.c_double
+            L.om_mode_lambda.argtypes = [P(Mat), C.c_int, C.c_double]
+            L.om_mode_velocity.restype = C.c_double
+            L.om_mode_velocity.argtypes = [P(Mat), C.c_int, C.c_double]
+            L.om_envelope_slowness.restype = C.c_double
+            L.om_envelope_slowness.argtypes = [P(Mat), C.c_int, C.c_double]
+            L.om_envelope_table.restype = None
+            L.om_envelope_table.argtypes = [P(Mat), C.c_int, P(C.c_double)]
             L.om_group_paper.restype = None
             L.om_group_paper.argtypes = [P(Mat), C.c_double, P(C.c_double), P(C.c_double)]
             L.om_group_exact.restype = None
@@ -111,7 +124,7 @@ def _ptr(a, ctype):
 def mat_from_voigt(c6, rho) -> Mat:
     """In-plane constants of the YZ plane (Sec. 3.2): c22, c23, c33, c44 of the 6x6 Voigt matrix."""
     c6 = np.asarray(c6, dtype=np.float64)
-    return Mat(c6[1, 1], c6[1, 2], c6[2, 2], c6[3, 3], float(rho))
+    return Mat(c6[1, 1], c6[1, 2], c6[2, 2], c6[3, 3], float(rho), c6[4, 4], c6[5, 5])
 
 
 def qp_lambda(m: Mat, theta: float) -> float:
@@ -120,6 +133,22 @@ def qp_lambda(m: Mat, theta: float) -> float:
 
 def phase_velocity(m: Mat, theta: float) -> float:
     return lib().om_phase_velocity(C.byref(m), float(theta))
+
+
+def mode_velocity(m: Mat, mode: int, theta: float) -> float:
+    """Phase speed of wave mode 0 (qP), 1 (qSV) or 2 (SH) at phase angle theta (Sec. 3.2, Sec. 7)."""
+    return lib().om_mode_velocity(C.byref(m), int(mode), float(theta))
+
+
+def envelope_slowness(m: Mat, mode: int, psi: float) -> float:
+    """First-arrival group slowness along psi: max over theta of cos(theta - psi) / v(theta)."""
+    return lib().om_envelope_slowness(C.byref(m), int(mode), float(psi))
+
+
+def envelope_table(m: Mat, mode: int) -> np.ndarray:
+    tab = np.empty(ENV_N, np.float64)
+    lib().om_envelope_table(C.byref(m), int(mode), _ptr(tab, C.c_double))
+    return tab
 
 
 def group_paper(m: Mat, phi: float):
@@ -151,7 +180,7 @@ def diamond_table() -> np.ndarray:
 class OMedium:
     """A medium on an nx x ny grid: per-node material index and orientation."""
 
-    def __init__(self, nx, ny, h, mat_id, theta, mats, group_model=GROUP_PAPER, vtable=0):
+    def __init__(self, nx, ny, h, mat_id, theta, mats, group_model=GROUP_PAPER, vtable=0, wave_mode=QP):
         self.nx, self.ny, self.h = int(nx), int(ny), float(h)
         self.mat_id = np.ascontiguousarray(mat_id, dtype=np.int32).reshape(ny * nx)
         self.theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(ny * nx)
@@ -159,15 +188,20 @@ class OMedium:
         self.mats = list(mats)
         self.group_model = int(group_model)
         self.vtable = int(vtable)
+        self.wave_mode = int(wave_mode)
+        # shear modes: every material's envelope table (the group speeds of [R20])
+        self.env = (np.concatenate([envelope_table(m, self.wave_mode) for m in mats]) if self.wave_mode
+                    else np.zeros(1))
         self.c = Medium(self.nx, self.ny, self.h, _ptr(self.mat_id, C.c_int32), _ptr(self.theta, C.c_double),
-                        self._mats, len(mats), self.group_model, self.vtable)
+                        self._mats, len(mats), self.group_model, self.vtable, self.wave_mode,
+                        _ptr(self.env, C.c_double))
 
     @classmethod
     def from_regions(cls, nx, ny, h, region_map, region_theta, region_material, mats, group_model=GROUP_PAPER,
-                     vtable=0):
+                     vtable=0, wave_mode=QP):
         rm = np.asarray(region_map).reshape(ny, nx).astype(np.int64)
         return cls(nx, ny, h, np.asarray(region_material)[rm], np.asarray(region_theta, np.float64)[rm], mats,
-                   group_model, vtable)
+                   group_model, vtable, wave_mode)
 
 
 def init_radius(M: OMedium, si: int, sj: int, r0: int):
@@ -290,8 +324,8 @@ def ray_gradient(M: OMedium, pts, region_of_node, nregions, eps=1e-6):
         tp, tm = M.theta.copy(), M.theta.copy()
         tp[reg == r] += eps
         tm[reg == r] -= eps
-        Mp = OMedium(M.nx, M.ny, M.h, M.mat_id, tp, M.mats, M.group_model, M.vtable)
-        Mm = OMedium(M.nx, M.ny, M.h, M.mat_id, tm, M.mats, M.group_model, M.vtable)
+        Mp = OMedium(M.nx, M.ny, M.h, M.mat_id, tp, M.mats, M.group_model, M.vtable, M.wave_mode)
+        Mm = OMedium(M.nx, M.ny, M.h, M.mat_id, tm, M.mats, M.group_model, M.vtable, M.wave_mode)
         g[r] = (path_time(Mp, pts) - path_time(Mm, pts)) / (2 * eps)
     return g
 
