@@ -144,6 +144,15 @@ typedef struct {
                                init_radius, level_radius, plane_step, ray_halfwidth and stop_radius stay in
                                original cells (the plan multiplies them by s); level_density is relative to
                                the fine grid. */
+    int wave_mode;          /* 0 = qP (default); 1 = qSV, the smaller in-plane eigenvalue of the Christoffel
+                               matrix; 2 = SH, its out-of-plane eigenvalue c66 cos^2 + c55 sin^2 (Sec. 7: S-wave
+                               times from the other eigenvalues of Sec. 3.2).  The local update takes the
+                               mode's phase speed.  For the shear modes group speeds (initialisation, fallback,
+                               rays) are the envelope 1/V(psi) = max over phase angles theta of
+                               cos(theta - psi) / v(theta) -- the eikonal's solution around a point source,
+                               single valued where the qSV ray surface has cusps -- tabulated per material at
+                               1/8 degree on the device and interpolated; group_model is then not used.  At
+                               most 4096 materials. */
 } alf_options;
 
 /* Fills `opt` with the defaults listed above.  Never fails. */
@@ -325,9 +334,11 @@ alf_status alf_plan_stats(alf_plan* plan, void* stream, alf_stats* out);
 alf_status alf_plan_autotune(alf_plan* plan, const double* region_theta, void* times, uint8_t* records,
                              void* stream);
 
-/* Velocity model on the device, for checks: out[k] = qP phase speed (kind 0)
- * or group speed (kind 1, model `group_model`) of material *mat (host) at
- * angle angles[k] relative to the material axis, computed in `precision`.
+/* Velocity model on the device, for checks: out[k] = phase speed (kind 0, 2,
+ * 4) or group speed (kind 1, 3, 5) of the qP (kinds 0, 1), qSV (2, 3) or SH
+ * (4, 5) mode of material *mat (host) at angle angles[k] relative to the
+ * material axis, computed in `precision`; qP group speeds by `group_model`,
+ * shear group speeds by the envelope table (see alf_options.wave_mode).
  *  angles, out  device double arrays of n entries */
 alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, int group_model, int precision,
                              const double* angles, double* out, int n, void* stream);

@@ -159,7 +159,7 @@ void om_envelope_table(const om_mat* m, int mode, double* tab)
     for (int k = 0; k < ENV_N; ++k) tab[k] = om_envelope_slowness(m, mode, k * M_PI / (ENV_N - 1));
 }
 
-static double envelope_speed(const double* tab, double psi)
+double om_envelope_speed(const double* tab, double psi)
 {
     double deg = psi * 180.0 / M_PI;
     deg -= 180.0 * floor(deg / 180.0); /* [0, 180) */
@@ -305,7 +305,7 @@ double om_group_speed(const om_mat* m, int model, double dir, double theta_mat)
 /* The medium's group speed of material `mat` along dir: the qP models above, or the shear modes' table. */
 static double med_group_speed(const om_medium* M, int mat, double dir, double theta_mat)
 {
-    if (M->wave_mode != 0) return envelope_speed(M->env + (size_t)mat * ENV_N, dir - theta_mat);
+    if (M->wave_mode != 0) return om_envelope_speed(M->env + (size_t)mat * ENV_N, dir - theta_mat);
     return om_group_speed(&M->mats[mat], M->group_model, dir, theta_mat);
 }
 

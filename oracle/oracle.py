@@ -75,6 +75,8 @@ def lib():
             L.om_envelope_slowness.argtypes = [P(Mat), C.c_int, C.c_double]
             L.om_envelope_table.restype = None
             L.om_envelope_table.argtypes = [P(Mat), C.c_int, P(C.c_double)]
+            L.om_envelope_speed.restype = C.c_double
+            L.om_envelope_speed.argtypes = [P(C.c_double), C.c_double]
             L.om_group_paper.restype = None
             L.om_group_paper.argtypes = [P(Mat), C.c_double, P(C.c_double), P(C.c_double)]
             L.om_group_exact.restype = None
@@ -149,6 +151,12 @@ def envelope_table(m: Mat, mode: int) -> np.ndarray:
     tab = np.empty(ENV_N, np.float64)
     lib().om_envelope_table(C.byref(m), int(mode), _ptr(tab, C.c_double))
     return tab
+
+
+def mode_group_speed(m: Mat, mode: int, psi: float) -> float:
+    """Group speed of a shear mode along psi from the material axis: the envelope table, interpolated [R20]."""
+    tab = envelope_table(m, mode)
+    return lib().om_envelope_speed(_ptr(tab, C.c_double), float(psi))
 
 
 def group_paper(m: Mat, phi: float):
@@ -360,11 +368,12 @@ def adjoint(M: OMedium, frozen, tau, rec, order, seeds, src, region, nregions, g
     return g
 
 
-def misfit_and_gradient(wl, sample, theta, t_obs, r0=2, group_model=0):
+def misfit_and_gradient(wl, sample, theta, t_obs, r0=2, group_model=0, wave_mode=QP):
     """L = sum over sources and receivers of (T - T_obs)^2 and dL/dtheta (oracle), for one sample."""
     s = wl.samples[sample]
     mats = [mat_from_voigt(c6, rho) for c6, rho in wl.materials]
-    M = OMedium.from_regions(s.nx, s.ny, s.h, s.region_map, theta, wl.region_material, mats, group_model)
+    M = OMedium.from_regions(s.nx, s.ny, s.h, s.region_map, theta, wl.region_material, mats, group_model,
+                             wave_mode=wave_mode)
     region = np.asarray(s.region_map, np.int32).reshape(-1)
     L = 0.0
     grad = np.zeros(len(theta), np.float64)

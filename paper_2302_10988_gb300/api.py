@@ -211,12 +211,17 @@ class Plan:
         return self.options
 
 
-def eval_velocity(c6, rho, angles, kind="phase", group="paper", precision="fp64", device=0):
-    """Device velocity model at angles (radians, relative to the material axis) -> numpy array."""
+MODES = {"qP": 0, "qSV": 1, "SH": 2}
+
+
+def eval_velocity(c6, rho, angles, kind="phase", group="paper", precision="fp64", device=0, mode="qP"):
+    """Device velocity model at angles (radians, relative to the material axis) -> numpy array; `mode` is the
+    wave mode (qP, qSV, SH)."""
     ctx = context(device)
     a = torch.as_tensor(np.asarray(angles, np.float64), device=torch.device("cuda", device)).contiguous()
     out = torch.empty_like(a)
-    B.alf_eval_velocity(ctx, _material(c6, rho), 0 if kind == "phase" else 1, GROUP[group], PRECISIONS[precision],
+    k = 2 * MODES[mode] + (0 if kind == "phase" else 1)
+    B.alf_eval_velocity(ctx, _material(c6, rho), k, GROUP[group], PRECISIONS[precision],
                         C.c_void_p(a.data_ptr()), C.c_void_p(out.data_ptr()), a.numel(),
                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()

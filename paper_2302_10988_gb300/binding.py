@@ -46,7 +46,8 @@ class alf_options(C.Structure):
                 ("max_ray_points", C.c_int), ("max_rounds", C.c_int), ("sweep", C.c_int),
                 ("ray_family", C.c_int), ("keep_records", C.c_int), ("band_cells", C.c_double),
                 ("use_graph", C.c_int), ("time_kernels", C.c_int), ("velocity_table", C.c_int),
-                ("cta_threads", C.c_int), ("cta_cluster", C.c_int), ("subgrid", C.c_int)]
+                ("cta_threads", C.c_int), ("cta_cluster", C.c_int), ("subgrid", C.c_int),
+                ("wave_mode", C.c_int)]
 
 
 class alf_stats(C.Structure):

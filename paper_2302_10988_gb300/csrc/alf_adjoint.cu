@@ -68,11 +68,11 @@ ALF_D void stencil_partials(int xA, int yA, int xB, int yB, int xC, int yC, T tA
         const T al = C * C * R.a22 + S * S * R.a44, ga = C * C * R.a44 + S * S * R.a33, be = C * S * R.a2344;
         const T dm = al - ga;
         const T Rr = sqrt_(dm * dm + T(4) * be * be);
-        L = T(0.5) * ((al + ga) + Rr);
+        L = T(0.5) * ((al + ga) + R.sig * Rr);
         T dC = T(2) * C * (R.a22 + R.a44), dS = T(2) * S * (R.a44 + R.a33);
         if (Rr > T(0)) {
-            dC += (dm * T(2) * C * (R.a22 - R.a44) + T(4) * be * S * R.a2344) / Rr;
-            dS += (dm * T(2) * S * (R.a44 - R.a33) + T(4) * be * C * R.a2344) / Rr;
+            dC += R.sig * (dm * T(2) * C * (R.a22 - R.a44) + T(4) * be * S * R.a2344) / Rr;
+            dS += R.sig * (dm * T(2) * S * (R.a44 - R.a33) + T(4) * be * C * R.a2344) / Rr;
         }
         dC *= T(0.5);
         dS *= T(0.5);

@@ -51,9 +51,12 @@ void dfree(void* p)
     if (p) cudaFree(p);
 }
 
-bool material_to_matd(const alf_material& m, MatD* out)
+// The constants of one material for wave mode `mode` (0 qP, 1 qSV, 2 SH; see MatD).  False for a
+// non-physical material.
+bool material_to_matd(const alf_material& m, int mode, MatD* out)
 {
     const double c22 = m.c[1][1], c23 = m.c[1][2], c33 = m.c[2][2], c44 = m.c[3][3], rho = m.rho;
+    const double c55 = m.c[4][4], c66 = m.c[5][5];
     if (!(rho > 0.0) || !std::isfinite(rho)) return false;
     for (double v : {c22, c23, c33, c44})
         if (!std::isfinite(v)) return false;
@@ -62,13 +65,36 @@ bool material_to_matd(const alf_material& m, MatD* out)
     // (qP and qSV lambda, Sec. 3.2) are > 0
     if (!(c22 > 0.0 && c33 > 0.0 && c44 > 0.0)) return false;
     if (!(c22 * c33 - c23 * c23 > 0.0)) return false;
+    *out = MatD{};
     out->a22 = c22 / rho;
     out->a23 = c23 / rho;
     out->a33 = c33 / rho;
     out->a44 = c44 / rho;
     out->iso = (c22 == c33 && c23 == c22 - 2.0 * c44) ? 1 : 0;
-    out->pad = 0;
+    if (mode == 1) {
+        out->sv = 1;
+        if (out->iso) out->a22 = c44 / rho;  // an isotropic solid's shear speed
+    } else if (mode == 2) {
+        // SH: the out-of-plane eigenvalue c66 cos^2 + c55 sin^2
+        if (!(c55 > 0.0 && c66 > 0.0) || !std::isfinite(c55) || !std::isfinite(c66)) return false;
+        out->a22 = c66 / rho;
+        out->a33 = c55 / rho;
+        out->a44 = 0.0;
+        out->a23 = std::sqrt(out->a22 * out->a33);
+        out->iso = c55 == c66 ? 1 : 0;
+    }
     return true;
+}
+
+// lambda / rho of a material's mode at phase angle th (host copy of the device formula)
+double mode_lambda_host(const MatD& m, double th)
+{
+    if (m.iso) return m.a22;
+    const double c = std::cos(th), sn = std::sin(th);
+    const double al = c * c * m.a22 + sn * sn * m.a44, ga = c * c * m.a44 + sn * sn * m.a33;
+    const double be = c * sn * (m.a23 + m.a44);
+    const double r = std::sqrt((al - ga) * (al - ga) + 4.0 * be * be);
+    return 0.5 * ((al + ga) + (m.sv ? -r : r));
 }
 
 
@@ -194,6 +220,7 @@ void alf_default_options(alf_options* o)
     o->use_graph = 1;
     o->time_kernels = 0;
     o->subgrid = 1;
+    o->wave_mode = 0;
 }
 
 alf_status alf_create(alf_ctx** out, int cuda_device)
@@ -221,7 +248,9 @@ alf_status alf_create(alf_ctx** out, int cuda_device)
     ctx->nsm = prop.multiProcessorCount;
     ctx->cc_major = prop.major;
     ctx->cc_minor = prop.minor;
-    if (cudaMalloc((void**)&ctx->d_scratch_mat, sizeof(MatD)) != cudaSuccess) {
+    if (cudaMalloc((void**)&ctx->d_scratch_mat, sizeof(MatD)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_scratch_env, sizeof(double) * ALF_ENV_N) != cudaSuccess) {
+        dfree(ctx->d_scratch_mat);
         delete ctx;
         return ALF_ERR_OOM;
     }
@@ -234,6 +263,7 @@ alf_status alf_destroy(alf_ctx* ctx)
     if (!ctx) return ALF_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     dfree(ctx->d_scratch_mat);
+    dfree(ctx->d_scratch_env);
     delete ctx;
     return ALF_OK;
 }
@@ -268,6 +298,7 @@ static void plan_free(alf_plan* p)
     dfree(p->d_map);
     dfree(p->d_region_mat);
     dfree(p->d_mats);
+    dfree(p->d_env);
     dfree(p->d_h);
     dfree(p->d_rec);
     dfree(p->d_regions);
@@ -325,6 +356,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (opt.plane_step < 1 || opt.plane_step > 16 || opt.ray_halfwidth < 1 || opt.ray_halfwidth > 16 ||
         !(opt.stop_radius > 0.0) || opt.max_ray_points < 2 || opt.max_ray_points > (1 << 20))
         return fail(ctx, ALF_ERR_INVALID_ARG, "ray options out of range");
+    if (opt.wave_mode < 0 || opt.wave_mode > 2) return fail(ctx, ALF_ERR_INVALID_ARG, "wave_mode must be 0, 1 or 2");
     if (opt.subgrid == 0) opt.subgrid = 1;  // a zeroed options struct means no refinement
     if (opt.subgrid < 1 || opt.subgrid > 21 || opt.subgrid % 2 == 0)
         return fail(ctx, ALF_ERR_INVALID_ARG, "subgrid must be an odd number in 1..21");
@@ -357,6 +389,8 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
         return fail(ctx, ALF_ERR_INVALID_ARG, "more than 65536 materials need region_material32");
     if (opt.velocity_table && g->nmaterials > 65536)
         return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table: at most 65536 materials");
+    if (opt.wave_mode != 0 && g->nmaterials > 4096)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "shear wave modes: at most 4096 materials");
     std::vector<uint32_t> rmat32(g->nregions);
     for (int r = 0; r < g->nregions; ++r)
         rmat32[r] = g->region_material32 ? g->region_material32[r] : g->region_material[r];
@@ -417,7 +451,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     }
     std::vector<MatD> mats(g->nmaterials);
     for (int m = 0; m < g->nmaterials; ++m)
-        if (!material_to_matd(g->materials[m], &mats[m]))
+        if (!material_to_matd(g->materials[m], opt.wave_mode, &mats[m]))
             return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "material %d: rho <= 0, non-finite or non-positive c", m);
     for (int r = 0; r < g->nregions; ++r)
         if (rmat32[r] >= (uint32_t)g->nmaterials)
@@ -478,16 +512,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // (a coarser scan when every node has its own material: the bound only sets the band width)
     const int nang = mats.size() > 4096 ? 36 : 180;
     for (const MatD& m : mats)
-        for (int k = 0; k < nang; ++k) {
-            const double th = k * 3.141592653589793 / nang, c = std::cos(th), sn = std::sin(th);
-            double lam = m.a22;
-            if (!m.iso) {
-                const double al = c * c * m.a22 + sn * sn * m.a44, ga = c * c * m.a44 + sn * sn * m.a33;
-                const double be = c * sn * (m.a23 + m.a44);
-                lam = 0.5 * ((al + ga) + std::sqrt((al - ga) * (al - ga) + 4.0 * be * be));
-            }
-            vmax = std::max(vmax, std::sqrt(lam));
-        }
+        for (int k = 0; k < nang; ++k) vmax = std::max(vmax, std::sqrt(mode_lambda_host(m, k * 3.141592653589793 / nang)));
     for (int b = 0; b < p->B; ++b)
         for (int s = 0; s < p->S; ++s) {
             FieldDesc fd{};
@@ -612,6 +637,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     ALLOC(p->d_map, p->total_map);
     ALLOC(p->d_region_mat, (size_t)p->R);
     ALLOC(p->d_mats, (size_t)p->nmat);
+    if (opt.wave_mode != 0) ALLOC(p->d_env, (size_t)p->nmat * ALF_ENV_N);
     ALLOC(p->d_h, (size_t)p->B);
     ALLOC(p->d_rec, (size_t)p->B * p->Rr * 2);
     ALLOC(p->d_q, 1);
@@ -659,22 +685,20 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     if (e == cudaSuccess) e = up(p->d_bm_off, bm_off.data(), bm_off.size() * sizeof(size_t));
     if (e == cudaSuccess) e = up(p->d_region_mat, rmat32.data(), (size_t)p->R * sizeof(uint32_t));
     if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
+    if (e == cudaSuccess && opt.wave_mode != 0) {
+        // shear modes: every material's envelope table on the device, then the materials point at theirs
+        e = launch_env_table(p->d_mats, p->nmat, p->d_env, nullptr);
+        for (int m = 0; m < p->nmat; ++m) mats[m].env = p->d_env + (size_t)m * ALF_ENV_N;
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = up(p->d_mats, mats.data(), mats.size() * sizeof(MatD));
+    }
     if (e == cudaSuccess && opt.velocity_table) {
         // phase speed of every material at 0..180 degrees from its axis (the qP eigenvalue of the rotated
         // Christoffel matrix, Sec. 3.2)
         std::vector<double> t64((size_t)p->nmat * ALF_VTAB_N);
         for (int m = 0; m < p->nmat; ++m)
-            for (int k = 0; k < ALF_VTAB_N; ++k) {
-                const MatD& q = mats[m];
-                double lam = q.a22;
-                if (!q.iso) {
-                    const double th = k * 3.141592653589793 / 180.0, c = std::cos(th), sn = std::sin(th);
-                    const double al = c * c * q.a22 + sn * sn * q.a44, ga = c * c * q.a44 + sn * sn * q.a33;
-                    const double be = c * sn * (q.a23 + q.a44);
-                    lam = 0.5 * ((al + ga) + std::sqrt((al - ga) * (al - ga) + 4.0 * be * be));
-                }
-                t64[(size_t)m * ALF_VTAB_N + k] = std::sqrt(lam);
-            }
+            for (int k = 0; k < ALF_VTAB_N; ++k)
+                t64[(size_t)m * ALF_VTAB_N + k] = std::sqrt(mode_lambda_host(mats[m], k * 3.141592653589793 / 180.0));
         e = up(p->d_vtab64, t64.data(), t64.size() * sizeof(double));
         if (e == cudaSuccess) {
             if (opt.precision == ALF_FP64) {
@@ -1159,18 +1183,25 @@ alf_status alf_eval_velocity(alf_ctx* ctx, const alf_material* mat, int kind, in
                              const double* angles, double* out, int n, void* stream)
 {
     if (!ctx) return ALF_ERR_INVALID_ARG;
-    if (!mat || !angles || !out || n < 0 || (kind != 0 && kind != 1) ||
+    if (!mat || !angles || !out || n < 0 || kind < 0 || kind > 5 ||
         (group_model != ALF_GROUP_PAPER && group_model != ALF_GROUP_EXACT) ||
         (precision != ALF_FP32 && precision != ALF_FP64))
         return fail(ctx, ALF_ERR_INVALID_ARG, "alf_eval_velocity: bad argument");
+    const int mode = kind / 2;
     MatD m;
-    if (!material_to_matd(*mat, &m)) return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "alf_eval_velocity: material");
+    if (!material_to_matd(*mat, mode, &m)) return fail(ctx, ALF_ERR_NONPHYSICAL_MATERIAL, "alf_eval_velocity: material");
     ALF_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = as_stream(stream);
     ALF_CUDA(ctx, cudaMemcpyAsync(ctx->d_scratch_mat, &m, sizeof(MatD), cudaMemcpyHostToDevice, st));
+    if (mode != 0) {
+        // the shear modes' group speeds come from the material's envelope table
+        ALF_CUDA(ctx, launch_env_table(ctx->d_scratch_mat, 1, ctx->d_scratch_env, st));
+        m.env = ctx->d_scratch_env;
+        ALF_CUDA(ctx, cudaMemcpyAsync(ctx->d_scratch_mat, &m, sizeof(MatD), cudaMemcpyHostToDevice, st));
+    }
     ALF_CUDA(ctx, cudaStreamSynchronize(st));
     if (n == 0) return ALF_OK;
-    ALF_CUDA(ctx, launch_eval_velocity(ctx->d_scratch_mat, kind, group_model, precision, angles, out, n, st));
+    ALF_CUDA(ctx, launch_eval_velocity(ctx->d_scratch_mat, kind % 2, group_model, precision, angles, out, n, st));
     return ALF_OK;
 }
 

@@ -32,16 +32,25 @@ struct RegionP {
     T fb[4];
     T dfb[4];  // d fb / d theta (used by the adjoint)
     T h;
+    T sig;     // root of the in-plane Christoffel block: +1 the larger (qP; SH by its constants), -1 the smaller (qSV)
     int iso;
     int pad;
-    const T* vtab;  // velocity-table mode: qP phase speed of the region's material at 0..180 degrees, else null
+    const T* vtab;  // velocity-table mode: phase speed of the region's material at 0..180 degrees, else null
 };
 
-struct MatD {   // per material, FP64, c / rho
+// Per material, FP64, c / rho, for the plan's wave mode (Sec. 3.2; Sec. 7 for the shear modes):
+//  qP   the YZ-plane constants, larger root;
+//  qSV  the same constants, smaller root (sv = 1); an isotropic material keeps its shear lambda in a22;
+//  SH   lambda = a66 cos^2 + a55 sin^2, written as the larger root of a block whose roots are a66 cos^2 +
+//       a55 sin^2 and 0: a22 = a66, a33 = a55, a44 = 0, a23 = sqrt(a66 a55).
+// env: for the shear modes, ALF_ENV_N envelope slownesses of the material (group speeds), else null.
+struct MatD {
     double a22, a23, a33, a44;
     int iso;
-    int pad;
+    int sv;
+    const double* env;
 };
+#define ALF_ENV_N 1441  // envelope slowness at 0, 1/8, ..., 180 degrees from the material axis
 
 // ---------------------------------------------------------------------------
 // Diamond slots: (-1,0) (1,0) (0,-1) (0,1) (-1,-1) (1,-1) (-1,1) (1,1)
@@ -134,7 +143,7 @@ ALF_D T phase_L(const RegionP<T>& R, T ux, T uy)
     const T ga = CC * R.a44 + SS * R.a33;
     const T be = C * S * R.a2344;
     const T dm = al - ga;
-    return T(0.5) * ((al + ga) + sqrt_(dm * dm + T(4) * be * be));
+    return T(0.5) * ((al + ga) + R.sig * sqrt_(dm * dm + T(4) * be * be));
 }
 
 ALF_D float div_(float a, float b) { return __fdividef(a, b); }
@@ -395,7 +404,21 @@ __device__ inline double qp_lambda64(const MatD& m, double c, double s)  // c, s
     const double ga = c * c * m.a44 + s * s * m.a33;
     const double be = c * s * (m.a23 + m.a44);
     const double dm = al - ga;
-    return 0.5 * ((al + ga) + sqrt(dm * dm + 4.0 * be * be));
+    const double r = sqrt(dm * dm + 4.0 * be * be);
+    return 0.5 * ((al + ga) + (m.sv ? -r : r));
+}
+
+// Shear modes: the group speed from the material's table of envelope slownesses (linear in slowness between
+// the entries at multiples of 1/8 degree; 180-degree symmetric).
+__device__ inline double env_speed64(const double* tab, double phi)
+{
+    double deg = phi * (180.0 / 3.141592653589793);
+    deg -= 180.0 * floor(deg / 180.0);
+    const double u = deg * ((ALF_ENV_N - 1) / 180.0);
+    int k = (int)floor(u);
+    k = k < 0 ? 0 : (k > ALF_ENV_N - 2 ? ALF_ENV_N - 2 : k);
+    const double f = u - k;
+    return 1.0 / ((1.0 - f) * tab[k] + f * tab[k + 1]);
 }
 
 // The paper's inversion (Sec. 3.2): find the phase angle theta whose qP
@@ -503,6 +526,7 @@ __device__ inline double group_exact64(const MatD& m, double phi)
 
 __device__ inline double group_speed64(const MatD& m, int model, double phi)
 {
+    if (m.env) return env_speed64(m.env, phi);
     return model == 1 ? group_exact64(m, phi) : group_paper64(m, phi);
 }
 
@@ -511,6 +535,7 @@ __device__ inline double group_speed64(const MatD& m, int model, double phi)
 // near the axes where the 0.01-degree rounding applies.
 __device__ inline float group_paper32(const MatD& m, float a22, float a33, float a44, float a2344, double phi)
 {
+    if (m.env) return (float)env_speed64(m.env, phi);
     if (m.iso) return sqrtf(a22);
     const float kPi = 3.14159265358979f;
     float deg = float(phi * (180.0 / 3.141592653589793));

@@ -67,6 +67,8 @@ cudaError_t launch_prep_regions(int precision, const MatD* mats, const uint32_t*
                                 const double* h, int nsamples, int nregions, int group_model, void* regions_out,
                                 cudaStream_t st, const void* vtab = nullptr);
 cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t st);
+// the shear modes' group slownesses: ALF_ENV_N entries per material (mats[].env ignored)
+cudaError_t launch_env_table(const MatD* mats, int nmat, double* tab, cudaStream_t st);
 // records `code` in q->error unless an earlier failure is recorded there (one tiny launch)
 cudaError_t launch_set_status(QueueState* q, unsigned code, cudaStream_t st);
 // streaming multiprocessors of the current device (queried once per device)
@@ -205,6 +207,7 @@ struct alf_ctx {
     int cc_major = 0, cc_minor = 0;
     std::string err;
     alf::MatD* d_scratch_mat = nullptr;
+    double* d_scratch_env = nullptr;  // one material's envelope table (alf_eval_velocity)
 };
 
 struct alf_plan {
@@ -233,6 +236,7 @@ struct alf_plan {
     void* d_vtab = nullptr;          // velocity tables of the plan precision (option velocity_table)
     double* d_vtab64 = nullptr;      // the same in FP64, for the FP64 check
     void* d_regions_rays = nullptr;  // RegionP<T> of the ray tracer (its own copy: rays may overlap the others)
+    double* d_env = nullptr;         // shear modes: ALF_ENV_N envelope slownesses per material
     // sweep workspace
     unsigned* d_list0 = nullptr;
     unsigned* d_list1 = nullptr;

@@ -63,6 +63,7 @@ __global__ void prep_regions_kernel(const MatD* mats, const uint32_t* region_mat
                         lens[cls] * hb / group_speed64(m, group_model, dirs[cls] - th + e)) / (2.0 * e));
     }
     R.h = T(hb);
+    R.sig = m.sv ? T(-1) : T(1);
     R.iso = m.iso;
     R.pad = 0;
     R.vtab = vtab ? vtab + (size_t)region_mat[r] * ALF_VTAB_N : nullptr;
@@ -128,6 +129,65 @@ cudaError_t launch_fill_inf(int precision, void* times, size_t n, cudaStream_t s
     if (grid < 1) grid = 1;
     if (precision == ALF_FP64) fill_inf_kernel<double><<<grid, 256, 0, st>>>((double*)times, n);
     else fill_inf_kernel<float><<<grid, 256, 0, st>>>((float*)times, n);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// env_table: for the shear modes, the group slowness of every material along the angles 0, 1/8, ..., 180
+// degrees from its axis, as the support function of its slowness curve, max over phase angles theta of
+// cos(theta - psi) / v(theta) (Sec. 7 with Sec. 3.2: the mode's eigenvalue gives v).  One thread per entry:
+// 4096 phase angles scanned over (psi - 90, psi + 90] degrees, then a golden-section search in the two scan
+// steps around the best.  In FP64, at plan creation.
+// ---------------------------------------------------------------------------
+__global__ void env_table_kernel(const MatD* mats, int nmat, double* tab)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nmat * ALF_ENV_N) return;
+    MatD m = mats[t / ALF_ENV_N];
+    m.env = nullptr;
+    const double kPi = 3.141592653589793;
+    const double psi = (t % ALF_ENV_N) * (kPi / (ALF_ENV_N - 1));
+    auto g = [&](double th) {
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        return cos(th - psi) * rsqrt(qp_lambda64(m, cs, sn));
+    };
+    constexpr int NS = 4096;
+    const double step = kPi / NS;
+    double best = -1.0, bt = psi;
+    for (int j = 1; j <= NS; ++j) {
+        const double th = psi - 0.5 * kPi + j * step, v = g(th);
+        if (v > best) {
+            best = v;
+            bt = th;
+        }
+    }
+    double lo = bt - step, hi = bt + step;
+    const double r = 0.6180339887498949;
+    double x1 = hi - r * (hi - lo), x2 = lo + r * (hi - lo), g1 = g(x1), g2 = g(x2);
+    for (int it = 0; it < 90; ++it) {
+        if (g1 < g2) {
+            lo = x1;
+            x1 = x2;
+            g1 = g2;
+            x2 = lo + r * (hi - lo);
+            g2 = g(x2);
+        } else {
+            hi = x2;
+            x2 = x1;
+            g2 = g1;
+            x1 = hi - r * (hi - lo);
+            g1 = g(x1);
+        }
+    }
+    tab[t] = fmax(best, fmax(g1, g2));
+}
+
+cudaError_t launch_env_table(const MatD* mats, int nmat, double* tab, cudaStream_t st)
+{
+    const int n = nmat * ALF_ENV_N;
+    env_table_kernel<<<(n + 127) / 128, 128, 0, st>>>(mats, nmat, tab);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1103,6 +1163,7 @@ __global__ void eval_velocity_kernel(const MatD* mat, int kind, int group_model,
             R.a2344 = float(m.a23 + m.a44);
             R.cth = 1.0f;
             R.sth = 0.0f;
+            R.sig = m.sv ? -1.0f : 1.0f;
             R.iso = m.iso;
             R.vtab = nullptr;  // the run-time Christoffel solve
             // a unit wavefront direction u whose normal (-u_y, u_x) is at angle a
