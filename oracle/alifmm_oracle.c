@@ -104,9 +104,12 @@ double om_phase_velocity(const om_mat* m, double theta)
  * cos^2(theta) c66 + sin^2(theta) c55 (eigenvector (1, 0, 0)). */
 double om_mode_lambda(const om_mat* m, int mode, double theta)
 {
+    if (mode == 0) return om_qp_lambda(m, theta);
+    /* the isotropic short-cut of Sec. 3.2 for the shear modes: the shear constant in every direction */
+    if (mode == 1 && mat_is_isotropic(m)) return m->c44;
+    if (mode == 2 && m->c55 == m->c66) return m->c66;
     double c = cos(theta), s = sin(theta);
     if (mode == 2) return c * c * m->c66 + s * s * m->c55;
-    if (mode == 0) return om_qp_lambda(m, theta);
     double alpha = c * c * m->c22 + s * s * m->c44;
     double beta = c * s * (m->c23 + m->c44);
     double gamma = c * c * m->c44 + s * s * m->c33;
@@ -126,6 +129,9 @@ double om_mode_velocity(const om_mat* m, int mode, double theta)
  * around the best one. */
 double om_envelope_slowness(const om_mat* m, int mode, double psi)
 {
+    /* an isotropic mode (qSV of an isotropic solid, SH with c55 = c66) has the circle 1 / v */
+    if ((mode == 1 && mat_is_isotropic(m)) || (mode == 2 && m->c55 == m->c66))
+        return 1.0 / om_mode_velocity(m, mode, 0.0);
     const int n = 3600;
     const double step = M_PI / n;
     double best = -1.0, bt = psi;
@@ -305,7 +311,13 @@ double om_group_speed(const om_mat* m, int model, double dir, double theta_mat)
 /* The medium's group speed of material `mat` along dir: the qP models above, or the shear modes' table. */
 static double med_group_speed(const om_medium* M, int mat, double dir, double theta_mat)
 {
-    if (M->wave_mode != 0) return om_envelope_speed(M->env + (size_t)mat * ENV_N, dir - theta_mat);
+    if (M->wave_mode != 0) {
+        const om_mat* m = &M->mats[mat];
+        /* an isotropic mode travels at its phase speed in every direction */
+        if ((M->wave_mode == 1 && mat_is_isotropic(m)) || (M->wave_mode == 2 && m->c55 == m->c66))
+            return om_mode_velocity(m, M->wave_mode, 0.0);
+        return om_envelope_speed(M->env + (size_t)mat * ENV_N, dir - theta_mat);
+    }
     return om_group_speed(&M->mats[mat], M->group_model, dir, theta_mat);
 }
 

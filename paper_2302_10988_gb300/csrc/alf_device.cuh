@@ -526,6 +526,7 @@ __device__ inline double group_exact64(const MatD& m, double phi)
 
 __device__ inline double group_speed64(const MatD& m, int model, double phi)
 {
+    if (m.iso) return sqrt(m.a22);  // an isotropic mode travels at its phase speed in every direction
     if (m.env) return env_speed64(m.env, phi);
     return model == 1 ? group_exact64(m, phi) : group_paper64(m, phi);
 }
@@ -535,8 +536,8 @@ __device__ inline double group_speed64(const MatD& m, int model, double phi)
 // near the axes where the 0.01-degree rounding applies.
 __device__ inline float group_paper32(const MatD& m, float a22, float a33, float a44, float a2344, double phi)
 {
-    if (m.env) return (float)env_speed64(m.env, phi);
     if (m.iso) return sqrtf(a22);
+    if (m.env) return (float)env_speed64(m.env, phi);
     const float kPi = 3.14159265358979f;
     float deg = float(phi * (180.0 / 3.141592653589793));
     deg -= 180.0f * floorf(deg / 180.0f);

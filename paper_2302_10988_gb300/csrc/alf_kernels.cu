@@ -146,6 +146,10 @@ __global__ void env_table_kernel(const MatD* mats, int nmat, double* tab)
     if (t >= nmat * ALF_ENV_N) return;
     MatD m = mats[t / ALF_ENV_N];
     m.env = nullptr;
+    if (m.iso) {  // the mode is isotropic in this material: the circle 1 / v
+        tab[t] = 1.0 / sqrt(m.a22);
+        return;
+    }
     const double kPi = 3.141592653589793;
     const double psi = (t % ALF_ENV_N) * (kPi / (ALF_ENV_N - 1));
     auto g = [&](double th) {

@@ -33,7 +33,7 @@ ALF_D double group_speed_T<double>(const MatD& m, const RegionP<double>& R, int 
 template <>
 ALF_D double group_speed_T<float>(const MatD& m, const RegionP<float>& R, int model, double phi)
 {
-    if (m.env) return env_speed64(m.env, phi);
+    if (m.env && !m.iso) return env_speed64(m.env, phi);
     if (model == 1) return group_exact64(m, phi);
     return (double)group_paper32(m, R.a22, R.a33, R.a44, R.a2344, phi);
 }

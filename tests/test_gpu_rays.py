@@ -135,3 +135,26 @@ def test_ray_gradient_matches_oracle(api, oracle, precision, tol):
     err = np.abs(g - g_o).max() / scale
     print(f"{precision} ray gradient: max |GPU - oracle| / max|oracle| = {err:.2e}")
     assert err < tol
+
+
+def test_ray_gradient_agrees_with_adjoint(api):
+    """Two routes to the same misfit gradient (Sec. 1: ray paths give gradients for inversion): the Fermat
+    gradient along the traced rays, paths held fixed (first order in the path, which is optimal), and the
+    discrete adjoint of the field solve.  They differ by the ray-vs-field time difference and the field's
+    discretisation, so they agree in direction and size, not to rounding."""
+    wl, truth = W.weld_adjoint(nsamples=3, n=96, rg=4, nsrc=8, nrec=8)
+    P = api.Plan(wl, precision="fp64", keep_records=1)
+    th = P.theta_tensor()
+    rec = P.new_records()
+    times, rt = P.solve(th, records=rec)
+    pts, npts, rtime, rst = P.trace_rays(th, times)
+    dT = 2.0 * (rt - 0.98 * rt.mean())  # a misfit seed that weights the receivers unevenly
+    g_adj = P.backward(th, times, rec, dT).cpu().numpy()
+    g_ray = P.ray_gradient(th, pts, npts, dT).cpu().numpy()
+    assert P.status() == 0 and (rst == 0).all()
+    for b in range(3):
+        a, r = g_adj[b, 1:], g_ray[b, 1:]
+        cos = float(a @ r / (np.linalg.norm(a) * np.linalg.norm(r)))
+        rel = float(np.linalg.norm(a - r) / np.linalg.norm(a))
+        print(f"sample {b}: cosine {cos:.4f}, relative difference {rel:.3f}")
+        assert cos > 0.95 and rel < 0.3

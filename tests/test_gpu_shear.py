@@ -46,8 +46,10 @@ def test_shear_velocity_model_on_device(api, oracle, mode):
     for c6, rho in (W.WELD_TI, ORTHO, W.PARENT_ISO):
         m = oracle.mat_from_voigt(c6, rho)
         v_o = np.array([oracle.mode_velocity(m, MODE[mode], a) for a in ang])
-        g_o = np.array([oracle.mode_group_speed(m, MODE[mode], a) for a in ang])
-        for prec, tv, tg in (("fp64", 1e-13, 1e-11), ("fp32", 2e-6, 1e-11)):
+        tab = oracle.envelope_table(m, MODE[mode])
+        g_o = np.array([oracle.lib().om_envelope_speed(tab.ctypes.data_as(oracle.C.POINTER(oracle.C.c_double)), a)
+                        for a in ang])
+        for prec, tv, tg in (("fp64", 1e-13, 1e-11), ("fp32", 2e-6, 2e-7)):
             v = api.eval_velocity(c6, rho, ang, "phase", precision=prec, mode=mode)
             g = api.eval_velocity(c6, rho, ang, "group", precision=prec, mode=mode)
             assert np.max(np.abs(v / v_o - 1)) < tv, (mode, prec)
