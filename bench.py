@@ -78,6 +78,8 @@ def _args():
                     help="profiling run: the whole step, or the travel-time solve alone")
     ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2, 3],
                     help="profiling run: sweep schedule (0: the library's choice)")
+    ap.add_argument("--band", type=float, default=1.5,
+                    help="profiling run: front band of the sweep in cell-crossing times")
     ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
                     help="profiling run: threads of a field's CTA in sweep 3 (0: the library's choice)")
     ap.add_argument("--profile-workload", default="batch", choices=["batch", "plain"],
@@ -209,7 +211,7 @@ def profile_run(args, wl, api, local):
     """One warm-up step and one step of the hot path with direct launches (no CUDA graph) on the default stream."""
     import torch
     full = args.profile_stages == "all"
-    P = api.Plan(wl, precision="fp32", device=local, keep_records=int(full), use_graph=0, band_cells=2.0,
+    P = api.Plan(wl, precision="fp32", device=local, keep_records=int(full), use_graph=0, band_cells=args.band,
                  sweep=args.sweep, cta_threads=args.cta_threads)
     th = P.theta_tensor()
     times, rect = P.new_times(), P.new_rec_times()

@@ -320,6 +320,7 @@ typedef struct {
                                   round (sweep 1) or the one field-resident sweep kernel (sweep 2, 3) */
     double eval_ms;            /* their device time, measured with CUDA events on the solve's stream */
     uint64_t kernel_launches;  /* kernel launches issued by the library so far (whole process) */
+    uint64_t dirty_entries;    /* dirty-list entries the rounds scanned (sweeps 2 and 3; 0 for sweep 1) */
 } alf_stats;
 alf_status alf_plan_stats(alf_plan* plan, void* stream, alf_stats* out);
 

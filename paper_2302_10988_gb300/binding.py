@@ -52,7 +52,8 @@ class alf_options(C.Structure):
 
 class alf_stats(C.Structure):
     _fields_ = [("node_evaluations", C.c_uint64), ("rounds", C.c_uint64), ("nodes", C.c_uint64),
-                ("eval_launches", C.c_uint64), ("eval_ms", C.c_double), ("kernel_launches", C.c_uint64)]
+                ("eval_launches", C.c_uint64), ("eval_ms", C.c_double), ("kernel_launches", C.c_uint64),
+                ("dirty_entries", C.c_uint64)]
 
 
 class alf_geometry(C.Structure):
@@ -215,7 +216,7 @@ def alf_plan_stats(ctx, plan, stream):
     _check(ctx, load().alf_plan_stats(plan, stream, C.byref(out)))
     return {"evaluations": int(out.node_evaluations), "rounds": int(out.rounds), "nodes": int(out.nodes),
             "eval_launches": int(out.eval_launches), "eval_ms": float(out.eval_ms),
-            "kernel_launches": int(out.kernel_launches)}
+            "kernel_launches": int(out.kernel_launches), "dirty_entries": int(out.dirty_entries)}
 
 
 def alf_plan_autotune(ctx, plan, theta_ptr, times_ptr, records_ptr, stream):

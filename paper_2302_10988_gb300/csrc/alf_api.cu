@@ -1061,6 +1061,7 @@ alf_status alf_plan_stats(alf_plan* p, void* stream, alf_stats* out)
     out->eval_launches = p->eval_launches;
     out->eval_ms = p->eval_ms;
     out->kernel_launches = launches_so_far();
+    out->dirty_entries = p->h_q->dirty;
     return ALF_OK;
 }
 

@@ -179,9 +179,9 @@ __global__ void __launch_bounds__(128) hier_kernel(HierLaunch a)
             // cell; later levels: the previous level's square)
             const int reach = (l == 0 ? d / 2 : a.rad[l - 1] * d) + 2;
             const unsigned nact = warp_seed_square(g, -a0, -b0, reach);
-            unsigned long long evals = 0ull;
+            unsigned long long evals = 0ull, scanned = 0ull;
             unsigned rounds = 0u;
-            if (!warp_sweep<T, VT>(g, nact, evals, rounds)) {
+            if (!warp_sweep<T, VT>(g, nact, evals, rounds, scanned)) {
                 if (lane == 0) atomicCAS(&a.q->error, 0u, (unsigned)ALF_ERR_NOT_CONVERGED);
                 return;
             }

@@ -30,7 +30,7 @@ struct QueueState {
     unsigned error;             // alf_status of the first device failure
     unsigned long long visits;  // node evaluations queued over all rounds
     unsigned long long rounds;  // rounds over all fields
-    unsigned long long pad;
+    unsigned long long dirty;   // dirty-list entries scanned over all rounds (field-resident schedules)
 };
 
 struct FimLaunch {

@@ -564,13 +564,14 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
         g.max_rounds = a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny);
         // first dirty set: the non-frozen nodes of the square around the frozen box
         const unsigned nact = warp_seed_square(g, fd.si, fd.sj, a.box + 2);
-        unsigned long long evals = 0ull;
+        unsigned long long evals = 0ull, scanned = 0ull;
         unsigned rounds = 0u;
-        const bool ok = warp_sweep<T, VT>(g, nact, evals, rounds);
+        const bool ok = warp_sweep<T, VT>(g, nact, evals, rounds, scanned);
         if (lane == 0) {
             if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
             atomicAdd(&a.q->visits, evals);
+            atomicAdd(&a.q->dirty, scanned);
             atomicMax(&a.q->rounds, (unsigned long long)rounds);
         }
         __syncwarp();
@@ -621,13 +622,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
         g.band = a.band_cells > 0.0 ? T(a.band_cells * fd.cell_time) : inf;
         g.max_rounds = a.max_rounds_per_node * (unsigned)(fd.nx + fd.ny);
         const unsigned nact = cta_seed_square<T, NT, CS>(g, fd.si, fd.sj, a.box + 2, S);
-        unsigned long long evals = 0ull;
+        unsigned long long evals = 0ull, scanned = 0ull;
         unsigned rounds = 0u;
-        const bool ok = cta_sweep<T, NT, VT, CS>(g, nact, evals, rounds, S);
+        const bool ok = cta_sweep<T, NT, VT, CS>(g, nact, evals, rounds, S, scanned);
         if (rank == 0 && threadIdx.x == 0) {
             if (!ok) set_error(a.q, ALF_ERR_NOT_CONVERGED);
             a.rounds[f] = rounds;
             atomicAdd(&a.q->visits, evals);
+            atomicAdd(&a.q->dirty, scanned);
             atomicMax(&a.q->rounds, (unsigned long long)rounds);
         }
         sweep_sync<CS>();

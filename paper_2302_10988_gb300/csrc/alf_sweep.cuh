@@ -79,7 +79,8 @@ ALF_D unsigned warp_seed_square(const WarpGrid<T>& g, int ci, int cj, int r)
 // rounds of one grid to its fixed point; returns the evaluations, writes the rounds taken, false when the
 // round cap was reached
 template <typename T, bool VT = false>
-ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds)
+ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds,
+                      unsigned long long& scanned)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const unsigned lane = threadIdx.x & 31u;
@@ -90,8 +91,10 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
     unsigned par = 0u;
     rounds = 0u;
     evals = 0ull;
+    scanned = 0ull;
     while (nact != 0u) {
         if (++rounds > g.max_rounds) return false;
+        scanned += nact;
         const unsigned* LA = par ? g.list1 : g.list0;
         unsigned* LB = par ? g.list0 : g.list1;
         // front time of the dirty set and the band limit
@@ -319,7 +322,7 @@ ALF_D unsigned cta_seed_square(const WarpGrid<T>& g, int ci, int cj, int r, CtaS
 
 template <typename T, int NT, bool VT = false, int CS = 1>
 ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& evals, unsigned& rounds,
-                     CtaSweepShared& S)
+                     CtaSweepShared& S, unsigned long long& scanned)
 {
     constexpr int NW = NT / 32;
     constexpr unsigned STRIDE = (unsigned)(NT * CS);
@@ -332,8 +335,10 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
     unsigned par = 0u;
     rounds = 0u;
     evals = 0ull;
+    scanned = 0ull;
     while (nact != 0u) {
         if (++rounds > g.max_rounds) return false;
+        scanned += nact;
         const unsigned* LA = par ? g.list1 : g.list0;
         unsigned* LB = par ? g.list0 : g.list1;
         // front time of the dirty set
