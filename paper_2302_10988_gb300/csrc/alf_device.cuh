@@ -176,6 +176,29 @@ ALF_HD constexpr int pa(int p) { constexpr int t[16] = {4, 6, 7, 5, 8, 11, 10, 9
 ALF_HD constexpr int pp(int p) { constexpr int t[16] = {2, 3, 1, 1, 4, 7, 5, 7, 3, 2, 2, 3, 0, 1, 1, 0}; return t[p]; }
 ALF_HD constexpr int pq(int p) { constexpr int t[16] = {0, 0, 3, 2, 6, 6, 4, 5, 7, 5, 4, 6, 6, 7, 5, 4}; return t[p]; }
 
+// Sec. 4.2, the travel time at D from the stencil pair p, in gradient form.  The plane through (A, tA),
+// (P, tP), (Q, tQ) has the time gradient g with g.(P - A) = tP - tA and g.(Q - A) = tQ - tA.  Its iso-line at
+// the middle time tB = min(tP, tQ) is the paper's wavefront EB (E on AC at time tB, C the later of P, Q), with
+// normal g; D lies |tau_lin(D) - tB| / |g| from it, tau_lin(D) = tA - g.A the plane's time at D.  So
+//   tau_D = tB + h |tau_lin(D) - tB| / (|g| v(g / |g|)) = tB + h |tau_lin(D) - tB| / sqrt(|g|^2 lambda(g) / rho),
+// the same time as the paper's construction, with no division: the inverse of (P - A, Q - A) is a constant of
+// the stencil (its determinant is +-1 or +-2), folded at compile time once p is.
+template <typename T, bool VT = false>
+ALF_D T pair_time(int p, T tA, T tP, T tQ, const RegionP<T>& R)
+{
+    const int xa = sdi(pa(p)), ya = sdj(pa(p));
+    const int e1x = sdi(pp(p)) - xa, e1y = sdj(pp(p)) - ya;
+    const int e2x = sdi(pq(p)) - xa, e2y = sdj(pq(p)) - ya;
+    const T inv = T(1) / T(e1x * e2y - e1y * e2x);
+    const T dP = tP - tA, dQ = tQ - tA;
+    const T gx = (T(e2y) * dP - T(e1y) * dQ) * inv;
+    const T gy = (T(e1x) * dQ - T(e2x) * dP) * inv;
+    const T tB = tP < tQ ? tP : tQ;
+    const T lin = tA - (T(xa) * gx + T(ya) * gy);
+    // phase_L takes the wavefront direction u, whose normal (-u_y, u_x) is g
+    return tB + R.h * abs_(lin - tB) * rsqrt_(phase_L<T, VT>(R, gy, -gx));
+}
+
 // Run-time lookups of the slot and pair tables (index known only at run time, e.g. from a
 // record): fields packed into 64-bit immediates and extracted with shifts, so that lanes with
 // different indices neither touch memory nor serialise on the constant cache.
@@ -306,9 +329,7 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         pv[p] = inf;
         if (rp[p] < 64 && tA < tP && tA < tQ) {
             const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
-            const int xB = m1 ? sdi(P) : sdi(Q), yB = m1 ? sdj(P) : sdj(Q);
-            const int xC = m1 ? sdi(Q) : sdi(P), yC = m1 ? sdj(Q) : sdj(P);
-            const T v = stencil_time<T, VT>(sdi(A), sdj(A), xB, yB, xC, yC, tA, tB, tC, R);
+            const T v = pair_time<T, VT>(p, tA, tP, tQ, R);
             if (v > tC) {
                 pv[p] = v;
                 pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));
@@ -534,15 +555,15 @@ __device__ inline double group_speed64(const MatD& m, int model, double phi)
 // FP32 paper inversion for the ray tracer; falls back to FP64 where the
 // root's acos argument is within 1e-2 of +-1 (ill-conditioned in FP32) and
 // near the axes where the 0.01-degree rounding applies.
-__device__ inline float group_paper32(const MatD& m, float a22, float a33, float a44, float a2344, double phi)
+__device__ inline float group_paper32(const MatD& m, float a22, float a33, float a44, float a2344, float phi)
 {
     if (m.iso) return sqrtf(a22);
-    if (m.env) return (float)env_speed64(m.env, phi);
+    if (m.env) return (float)env_speed64(m.env, (double)phi);
     const float kPi = 3.14159265358979f;
-    float deg = float(phi * (180.0 / 3.141592653589793));
+    float deg = phi * (180.0f / kPi);
     deg -= 180.0f * floorf(deg / 180.0f);
     const float k90 = 90.0f * rintf(deg / 90.0f);
-    if (fabsf(deg - k90) < 0.05f) return float(group_paper64(m, phi));
+    if (fabsf(deg - k90) < 0.05f) return float(group_paper64(m, (double)phi));
     const float ph = deg * (kPi / 180.0f);
     float s2p, c2p;
     sincosf(2.0f * ph, &s2p, &c2p);
@@ -550,7 +571,7 @@ __device__ inline float group_paper32(const MatD& m, float a22, float a33, float
     const float A = delta * s2p, B = -2.0f * a2344 * c2p, Cc = -kappa * s2p;
     const float Rr = sqrtf(A * A + B * B);
     const float q = Cc / Rr;
-    if (fabsf(q) > 0.99f) return float(group_paper64(m, phi));
+    if (fabsf(q) > 0.99f) return float(group_paper64(m, (double)phi));
     const float X0 = atan2f(B, A), dX = acosf(q);
     float cph, sph;
     sincosf(ph, &sph, &cph);

@@ -1178,7 +1178,7 @@ __global__ void eval_velocity_kernel(const MatD* mat, int kind, int group_model,
     } else {
         if (precision == ALF_FP64 || group_model == 1) out[k] = group_speed64(m, group_model, a);
         else
-            out[k] = (double)group_paper32(m, float(m.a22), float(m.a33), float(m.a44), float(m.a23 + m.a44), a);
+            out[k] = (double)group_paper32(m, float(m.a22), float(m.a33), float(m.a44), float(m.a23 + m.a44), (float)a);
     }
 }
 

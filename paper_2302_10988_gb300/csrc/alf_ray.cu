@@ -21,21 +21,20 @@
 
 namespace alf {
 
-template <typename T>
-ALF_D double group_speed_T(const MatD& m, const RegionP<T>& R, int model, double phi);
-
-template <>
-ALF_D double group_speed_T<double>(const MatD& m, const RegionP<double>& R, int model, double phi)
+// Group speed along the angle phi from the material axis, in the ray's precision: the FP32 path stays on the
+// FP32 pipe (the FP64 pipe runs at a small fraction of its rate) except where the inversion is ill-conditioned
+// near the axes, the EXACT model's Newton solve and the shear modes' FP64 table.
+ALF_D double group_speed_T(const MatD& m, const RegionP<double>& R, int model, double phi)
 {
+    (void)R;
     return group_speed64(m, model, phi);
 }
 
-template <>
-ALF_D double group_speed_T<float>(const MatD& m, const RegionP<float>& R, int model, double phi)
+ALF_D float group_speed_T(const MatD& m, const RegionP<float>& R, int model, float phi)
 {
-    if (m.env && !m.iso) return env_speed64(m.env, phi);
-    if (model == 1) return group_exact64(m, phi);
-    return (double)group_paper32(m, R.a22, R.a33, R.a44, R.a2344, phi);
+    if (m.env && !m.iso) return (float)env_speed64(m.env, (double)phi);
+    if (model == 1) return (float)group_exact64(m, (double)phi);
+    return group_paper32(m, R.a22, R.a33, R.a44, R.a2344, phi);
 }
 
 template <typename T>
@@ -54,25 +53,31 @@ struct RayCtx {
 template <typename T>
 ALF_D int node_at(const RayCtx<T>& c, T x, T y)
 {
-    int i = (int)floor((double)x + 0.5), j = (int)floor((double)y + 0.5);
+    int i = (int)floor(x + T(0.5)), j = (int)floor(y + T(0.5));
     i = min(max(i, 0), c.nx - 1);
     j = min(max(j, 0), c.ny - 1);
     return j * c.nx + i;
 }
 
-// direction angle of (sx, sy) relative to the orientation th: FP32 atan2 on the FP32 path (the
-// ray's own precision; the FP64 pipe is slow on this part), FP64 on the FP64 path
-ALF_D double rel_dir(float sx, float sy, double th) { return (double)(atan2f(sy, sx) - (float)th); }
-ALF_D double rel_dir(double sx, double sy, double th) { return atan2(sy, sx) - th; }
-
-// straight-ray time of length len (cells) along (sx, sy) through node n
-template <typename T>
-ALF_D T piece_time(const RayCtx<T>& c, int n, T len, T sx, T sy)
+// straight-ray time of length len (cells) along (sx, sy) through node n.  FP64: the direction angle relative
+// to the orientation as atan2 - theta; FP32: (sx, sy) rotated by the region's (cos, sin) of theta first, then
+// one atan2, and the time in FP32.
+ALF_D double piece_time(const RayCtx<double>& c, int n, double len, double sx, double sy)
 {
     const int r = c.map[c.map_off + n];
     const MatD& m = c.mats[c.region_mat[r]];  // by reference: no local copy for the FP64 fallbacks
-    const double V = group_speed_T<T>(m, c.regions[r], c.model, rel_dir(sx, sy, c.theta[r]));
-    return T((double)len * c.h / V);
+    const double V = group_speed_T(m, c.regions[r], c.model, atan2(sy, sx) - c.theta[r]);
+    return len * c.h / V;
+}
+
+ALF_D float piece_time(const RayCtx<float>& c, int n, float len, float sx, float sy)
+{
+    const int r = c.map[c.map_off + n];
+    const MatD& m = c.mats[c.region_mat[r]];
+    const RegionP<float>& R = c.regions[r];
+    const float phi = atan2f(sy * R.cth - sx * R.sth, sx * R.cth + sy * R.sth);
+    const float V = group_speed_T(m, R, c.model, phi);
+    return len * R.h / V;
 }
 
 // plane families: x = c, y = c, x - y = c, x + y = c; normal (fam_nx, fam_ny) and node step along the plane
@@ -108,6 +113,7 @@ __global__ void ray_kernel(RayLaunch a)
     const T x0r = T(a.rec_ij[((size_t)b * a.nrec + r) * 2]), y0r = T(a.rec_ij[((size_t)b * a.nrec + r) * 2 + 1]);
     // one plane walk from the receiver to the source; famsel -1: the set most perpendicular to the ray at
     // every step, 0..3: one fixed set (Sec. 5.1).  Returns the point count.
+    const T stop_r = T(a.stop_radius);
     auto walk = [&](int famsel, int& status) -> int {
     T bx = x0r, by = y0r;
     T dx = xt - bx, dy = yt - by;
@@ -118,7 +124,7 @@ __global__ void ray_kernel(RayLaunch a)
     status = 1;
     while (np < a.max_pts) {
         const T rx = xt - bx, ry = yt - by;
-        if (sqrt_(rx * rx + ry * ry) < T(a.stop_radius)) {
+        if (sqrt_(rx * rx + ry * ry) < stop_r) {
             pts[2 * np] = xt;
             pts[2 * np + 1] = yt;
             np++;
@@ -173,7 +179,7 @@ __global__ void ray_kernel(RayLaunch a)
         }
         const T stx = T(fam_tx(fam)), sty = T(fam_ty(fam));
         const T pc = fam == 0 ? py : px;
-        int p0 = (int)floor((double)pc + 0.5);
+        int p0 = (int)floor(pc + T(0.5));
         {
             // the window is centred on the part of the plane inside the grid (a set of planes nearly
             // parallel to the ray meets the ray's line far off the grid)

@@ -22,6 +22,18 @@ ALF_D unsigned long long warp_min(unsigned long long v)
 }
 
 
+// Which of the 12 diamond slots of node (i, j) lie inside the nx x ny grid: eight edge tests, combined per slot
+// (slot order as kSlotDi / kSlotDj), instead of four bounds tests per slot.
+struct SlotInGrid {
+    bool v[12];
+};
+ALF_D SlotInGrid slots_in_grid(int i, int j, int nx, int ny)
+{
+    const bool l1 = i >= 1, l2 = i >= 2, r1 = i + 1 < nx, r2 = i + 2 < nx;
+    const bool d1 = j >= 1, d2 = j >= 2, u1 = j + 1 < ny, u2 = j + 2 < ny;
+    return SlotInGrid{{l1, r1, d1, u1, l1 && d1, r1 && d1, l1 && u1, r1 && u1, l2, r2, d2, u2}};
+}
+
 // One grid swept by one warp: a field, or one level of the near-source hierarchy.
 template <typename T>
 struct WarpGrid {
@@ -131,12 +143,10 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
         for (unsigned e = lane; e < ne; e += 32u) {
             const unsigned n = g.el[e];
             const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+            const SlotInGrid in = slots_in_grid(i, j, nx, ny);
             T nb[12];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                const int ii = i + sdi(q), jj = j + sdj(q);
-                nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
-            }
+            for (int q = 0; q < 12; ++q) nb[q] = in.v[q] ? tf[(int)n + sdj(q) * nx + sdi(q)] : inf;
             const T old = tf[n];
             RegionP<T> R = g.reg[__ldg(g.map + n)];
             if (g.scale != T(1)) {
@@ -173,11 +183,11 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
                 if (changed || inband) {
                     const T lo = v < o ? v : o;
                     bool seeds_later = false;
+                    const SlotInGrid in = slots_in_grid(i, j, nx, ny);
 #pragma unroll
                     for (int q = 0; q < 12; ++q) {
-                        const int ii = i + sdi(q), jj = j + sdj(q);
-                        if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
-                            const T tm = tf[jj * nx + ii];
+                        if (in.v[q]) {
+                            const T tm = tf[(int)n + sdj(q) * nx + sdi(q)];
                             if (!neg_bit(tm)) {
                                 bool push = false;
                                 if (tm < inf) push = changed && lo <= tm;
@@ -397,12 +407,10 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
         for (unsigned e = tid; e < ne; e += STRIDE) {
             const unsigned n = g.el[e];
             const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
+            const SlotInGrid in = slots_in_grid(i, j, nx, ny);
             T nb[12];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                const int ii = i + sdi(q), jj = j + sdj(q);
-                nb[q] = (ii >= 0 && jj >= 0 && ii < nx && jj < ny) ? tf[jj * nx + ii] : inf;
-            }
+            for (int q = 0; q < 12; ++q) nb[q] = in.v[q] ? tf[(int)n + sdj(q) * nx + sdi(q)] : inf;
             const T old = tf[n];
             RegionP<T> R = g.reg[__ldg(g.map + n)];
             if (g.scale != T(1)) {
@@ -437,11 +445,11 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
                 if (changed || inband) {
                     const T lo = v < o ? v : o;
                     bool seeds_later = false;
+                    const SlotInGrid in = slots_in_grid(i, j, nx, ny);
 #pragma unroll
                     for (int q = 0; q < 12; ++q) {
-                        const int ii = i + sdi(q), jj = j + sdj(q);
-                        if (ii >= 0 && jj >= 0 && ii < nx && jj < ny) {
-                            const T tm = tf[jj * nx + ii];
+                        if (in.v[q]) {
+                            const T tm = tf[(int)n + sdj(q) * nx + sdi(q)];
                             if (!neg_bit(tm)) {
                                 bool push = false;
                                 if (tm < inf) push = changed && lo <= tm;
