@@ -14,7 +14,9 @@
 //             node (how many later nodes use it);
 //   (everything the sweep touches per node -- weights, lambda, its
 //   contribution lambda * dtau/dtheta, in-degree -- sits in one 32-byte
-//   record (64 bytes in FP64), one DRAM sector per node visit);
+//   record (64 bytes in FP64), one DRAM sector per node visit; a user's
+//   contribution and its release of a support node are one vector atomic
+//   on the adjacent (lambda, in-degree) pair in FP32);
 //   seed      lambda = dL/dT at the receivers;
 //   rounds    Kahn's order: a node whose users have all been processed is
 //             final; it adds lambda * weight to the nodes it used and releases
@@ -38,11 +40,25 @@ struct alignas(8 * sizeof(T)) AdjNode {
     T w[3];           // d tau_D / d tau of the supporting nodes (stencil A, B, C; fallback: w[0] = 1)
     T wt;             // d tau_D / d theta
     T lam;            // dL / d tau_D
+    T indeg;          // later nodes that use this one, not yet processed (a small integer, exact in T)
     T gn;             // lam * wt (the node's contribution to its region's gradient)
-    unsigned indeg;   // later nodes that use this one, not yet processed
-    unsigned pad;
+    T pad;
 };
 static_assert(sizeof(AdjNode<float>) == 32 && sizeof(AdjNode<double>) == 64, "one or two DRAM sectors per node");
+
+// A processed user hands its contribution to a support node and releases it: lam += c, indeg -= 1; returns
+// true when that was the last user (the support node is final).  FP32: one 8-byte vector atomic on the
+// adjacent (lam, indeg) pair, so the contribution and the release land together; FP64: two atomics.
+ALF_D bool release(AdjNode<float>* node, float c)
+{
+    const float2 old = atomicAdd(reinterpret_cast<float2*>(&node->lam), make_float2(c, -1.0f));
+    return old.y == 1.0f;
+}
+ALF_D bool release(AdjNode<double>* node, double c)
+{
+    atomicAdd(&node->lam, c);
+    return atomicAdd(&node->indeg, -1.0) == 1.0;
+}
 
 size_t adj_node_bytes(int precision) { return precision == ALF_FP64 ? sizeof(AdjNode<double>) : sizeof(AdjNode<float>); }
 
@@ -190,7 +206,7 @@ __global__ void adj_weights_kernel(AdjLaunch a)
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    if (k < ns) atomicAdd(&An[ms[k]].indeg, 1u);
+                    if (k < ns) atomicAdd(&An[ms[k]].indeg, T(1));
             }
             AdjNode<T>& r = An[n];
             r.w[0] = w0;
@@ -230,7 +246,7 @@ __global__ void adj_frontier_kernel(AdjLaunch a)
         unsigned cnt = 0;
         for (unsigned base = 0; base < N; base += 32u) {
             const unsigned n = base + lane;
-            const bool take = n < N && An[n].indeg == 0u;
+            const bool take = n < N && An[n].indeg == T(0);
             const unsigned bal = __ballot_sync(0xffffffffu, take);
             if (take) list[cnt + __popc(bal & ((1u << lane) - 1u))] = n;
             cnt += __popc(bal);
@@ -252,7 +268,7 @@ __global__ void adj_frontier_flat_kernel(AdjLaunch a)
         const unsigned N = (unsigned)(fd.nx * fd.ny);
         const AdjNode<T>* An = A + fd.node_off;
         for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
-            if (An[n].indeg == 0u) a.list[0][fd.node_off + atomicAdd(a.cnt + f, 1u)] = n;
+            if (An[n].indeg == T(0)) a.list[0][fd.node_off + atomicAdd(a.cnt + f, 1u)] = n;
     }
 }
 
@@ -309,11 +325,8 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
         unsigned* list = a.list[parity ^ 1] + fd.node_off;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            if (k < ns) {
-                atomicAdd(&An[ms[k]].lam, l * (k == 0 ? w0 : k == 1 ? w1 : w2));
-                __threadfence();
-                if (atomicSub(&An[ms[k]].indeg, 1u) == 1u) list[atomicAdd(nxt + lo, 1u)] = ms[k];
-            }
+            if (k < ns && release(&An[ms[k]], l * (k == 0 ? w0 : k == 1 ? w1 : w2)))
+                list[atomicAdd(nxt + lo, 1u)] = ms[k];
     }
 }
 
@@ -374,10 +387,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
                         const int ns = support_nodes(a.records[fd.node_off + n], i, j, nx, ny, ms);
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
-                            if (k < ns) atomicAdd(&An[ms[k]].lam, l * (k == 0 ? w0 : k == 1 ? w1 : w2));
-#pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            if (k < ns) fresh[k] = atomicSub(&An[ms[k]].indeg, 1u) == 1u;
+                            if (k < ns) fresh[k] = release(&An[ms[k]], l * (k == 0 ? w0 : k == 1 ? w1 : w2));
                     }
                 }
 #pragma unroll
@@ -423,7 +433,7 @@ __global__ void adj_reduce_kernel(AdjLaunch a, double* grad)
     const int N = fd.nx * fd.ny;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         // every node is released once its users are processed; one that was not sits on a cycle
-        if (An[n].indeg != 0u) adj_set_error(a.q, ALF_ERR_INCONSISTENT_RECORDS);
+        if (An[n].indeg != T(0)) adj_set_error(a.q, ALF_ERR_INCONSISTENT_RECORDS);
         const T v = An[n].gn;
         if (v == T(0)) continue;
         const int i = n % fd.nx, j = n / fd.nx;
