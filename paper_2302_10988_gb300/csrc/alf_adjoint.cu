@@ -334,6 +334,8 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
 // warp touches a field's node records, and the warp barrier at the end of a round orders a round's
 // contributions before the next round reads them (through L2: __ldcg).  With few regions the
 // warp sums the region gradients in shared memory as it goes.
+#define ADJ_U 4  // frontier entries per lane per pass of the field-resident adjoint
+
 template <typename T>
 __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad, int smem_regions)
 {
@@ -367,35 +369,60 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
             const unsigned* LA = par ? list1 : list0;
             unsigned* LB = par ? list0 : list1;
             unsigned nc = 0u;
-            for (unsigned base = 0; base < nact; base += 32u) {
-                const unsigned e = base + lane;
-                unsigned ms[3] = {0u, 0u, 0u};
-                bool fresh[3] = {false, false, false};
-                if (e < nact) {
-                    const unsigned n = LA[e];
-                    const T l = __ldcg(&An[n].lam);
-                    const T w0 = An[n].w[0], w1 = An[n].w[1], w2 = An[n].w[2];
-                    const T g = l * An[n].wt;
+            // up to ADJ_U entries per lane at once: their loads, then their releases, are independent, so a
+            // round costs about one chain of memory round trips instead of one per 32 entries
+            for (unsigned base = 0; base < nact; base += 32u * ADJ_U) {
+                unsigned nn[ADJ_U], ms[ADJ_U][3];
+                bool fresh[ADJ_U][3];
+                T l[ADJ_U], w[ADJ_U][3], g[ADJ_U];
+                int rec[ADJ_U];
+#pragma unroll
+                for (int u = 0; u < ADJ_U; ++u) {
+                    const unsigned e = base + 32u * u + lane;
+                    nn[u] = e < nact ? LA[e] : ~0u;
+                }
+#pragma unroll
+                for (int u = 0; u < ADJ_U; ++u) {
+                    l[u] = w[u][0] = w[u][1] = w[u][2] = g[u] = T(0);
+                    rec[u] = 255;
+                    if (nn[u] != ~0u) {
+                        const AdjNode<T>& r = An[nn[u]];
+                        l[u] = __ldcg(&r.lam);
+                        w[u][0] = r.w[0];
+                        w[u][1] = r.w[1];
+                        w[u][2] = r.w[2];
+                        g[u] = l[u] * r.wt;
+                        rec[u] = a.records[fd.node_off + nn[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < ADJ_U; ++u) {
+                    fresh[u][0] = fresh[u][1] = fresh[u][2] = false;
+                    ms[u][0] = ms[u][1] = ms[u][2] = 0u;
+                    if (nn[u] == ~0u) continue;
+                    const unsigned n = nn[u];
                     const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
                     const bool fz = frozen_at(fbits, a.box, fd, i, j);
                     if (smem_regions) {
-                        if (g != T(0)) atomicAdd(acc + (fz ? rsrc : (int)map[n]), (double)g);
+                        if (g[u] != T(0)) atomicAdd(acc + (fz ? rsrc : (int)map[n]), (double)g[u]);
                     } else {
-                        An[n].gn = g;
+                        An[n].gn = g[u];
                     }
                     if (!fz) {
-                        const int ns = support_nodes(a.records[fd.node_off + n], i, j, nx, ny, ms);
+                        const int ns = support_nodes(rec[u], i, j, nx, ny, ms[u]);
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
-                            if (k < ns) fresh[k] = release(&An[ms[k]], l * (k == 0 ? w0 : k == 1 ? w1 : w2));
+                            if (k < ns) fresh[u][k] = release(&An[ms[u][k]], l[u] * w[u][k]);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const unsigned b = __ballot_sync(FULL, fresh[k]);
-                    if (fresh[k]) LB[nc + __popc(b & below)] = ms[k];
-                    nc += __popc(b);
-                }
+                for (int u = 0; u < ADJ_U; ++u)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const unsigned b = __ballot_sync(FULL, fresh[u][k]);
+                        if (fresh[u][k]) LB[nc + __popc(b & below)] = ms[u][k];
+                        nc += __popc(b);
+                    }
             }
             __syncwarp();
             nact = nc;
