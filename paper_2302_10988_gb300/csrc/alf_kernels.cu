@@ -927,18 +927,21 @@ ALF_D bool box_frozen(const unsigned* bits, int box, const FieldDesc& fd, int i,
 template <typename T, bool VT>
 ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R, int& rec)
 {
-    int xA = 0, yA = 0, xB = 0, yB = 0, xC = 0, yC = 0, r = 255;
+    // the pair's geometry as FP64 constants chosen by predicated moves (no integer-to-FP64 conversion, which
+    // runs on the slow FP64 pipe); dxC, dyC: C - A
+    double xA = 0.0, yA = 0.0, xB = 0.0, yB = 0.0, dxC = 0.0, dyC = 0.0;
+    int r = 255;
     T tA = T(0), tB = T(0), tC = T(0);
 #pragma unroll
     for (int p = 0; p < 16; ++p)
         if (p == bp) {
             const bool m1 = t[pp(p)] <= t[pq(p)];
-            xA = sdi(pa(p));
-            yA = sdj(pa(p));
-            xB = m1 ? sdi(pp(p)) : sdi(pq(p));
-            yB = m1 ? sdj(pp(p)) : sdj(pq(p));
-            xC = m1 ? sdi(pq(p)) : sdi(pp(p));
-            yC = m1 ? sdj(pq(p)) : sdj(pp(p));
+            xA = double(sdi(pa(p)));
+            yA = double(sdj(pa(p)));
+            xB = m1 ? double(sdi(pp(p))) : double(sdi(pq(p)));
+            yB = m1 ? double(sdj(pp(p))) : double(sdj(pq(p)));
+            dxC = m1 ? double(sdi(pq(p)) - sdi(pa(p))) : double(sdi(pp(p)) - sdi(pa(p)));
+            dyC = m1 ? double(sdj(pq(p)) - sdj(pa(p))) : double(sdj(pp(p)) - sdj(pa(p)));
             tA = t[pa(p)];
             tB = m1 ? t[pp(p)] : t[pq(p)];
             tC = m1 ? t[pq(p)] : t[pp(p)];
@@ -949,7 +952,7 @@ ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R,
     // reciprocal square root instead of a square root and two divisions.  The differences of FP32
     // times are exact in FP64.
     const double num = (double)tB - (double)tA, den = (double)tC - (double)tA;
-    const double Ex = xA * den + num * (xC - xA), Ey = yA * den + num * (yC - yA);
+    const double Ex = xA * den + num * dxC, Ey = yA * den + num * dyC;
     const double ux = xB * den - Ex, uy = yB * den - Ey;
     const double cross = fabs(yB * Ex - xB * Ey);
     const double v = (double)tB + R.h * cross * rsqrt(phase_L<double, VT>(R, ux, uy));
