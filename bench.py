@@ -82,6 +82,9 @@ def _args():
                     help="profiling run: front band of the sweep in cell-crossing times")
     ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
                     help="profiling run: threads of a field's CTA in sweep 3 (0: the library's choice)")
+    ap.add_argument("--check", default="stream", choices=["fused", "stream"],
+                    help="FP64 check of the step: inside the solve (alf_solve_check64) or on a stream of its own "
+                         "after the solve (alf_check64 beside the rays and the adjoint)")
     ap.add_argument("--profile-workload", default="batch", choices=["batch", "plain"],
                     help="profiling run: the weld batch (--samples x 32 sources) or the plain single medium "
                          "(256 x 256 weld, 32 sources)")
@@ -218,9 +221,13 @@ def profile_run(args, wl, api, local):
     rec = P.new_records() if full else None
     t0 = time.perf_counter()
     for _ in range(2):
-        P.solve(th, times=times, rec_times=rect, records=rec)
+        if full and args.check == "fused":
+            P.solve_check64(th, times=times, rec_times=rect, records=rec)
+        else:
+            P.solve(th, times=times, rec_times=rect, records=rec)
         if full:
-            P.check64(th, times, rec)
+            if args.check != "fused":
+                P.check64(th, times, rec)
             P.trace_rays(th, times)
             P.backward(th, times, rec, 2.0 * rect)
     torch.cuda.synchronize()
@@ -318,16 +325,22 @@ def main():
     side = [torch.cuda.Stream(), torch.cuda.Stream()]
 
     def step(theta):
-        # after the solve, the FP64 check (FP64 pipe), the rays (FP32) and the adjoint (memory) are
-        # independent: they run on three streams and the step ends when all three have
+        # the FP64 check (FP64 pipe) runs inside the solve, each field checked by the CTA that solved it
+        # (--check fused), or after the solve on a stream of its own; the rays (FP32) and the adjoint (memory)
+        # are independent of each other and of the check: they run on two more streams, and the step ends
+        # when all have
         cur = torch.cuda.current_stream()
-        P.solve(theta, times=times, rec_times=rect, records=rec)
+        if args.check == "fused":
+            _, _, mr, fl = P.solve_check64(theta, times=times, rec_times=rect, records=rec)
+        else:
+            P.solve(theta, times=times, rec_times=rect, records=rec)
         solved = torch.cuda.Event()
         solved.record(cur)
         for s in side:
             s.wait_event(solved)
-        with torch.cuda.stream(side[0]):
-            mr, fl = P.check64(theta, times, rec)
+        if args.check != "fused":
+            with torch.cuda.stream(side[0]):
+                mr, fl = P.check64(theta, times, rec)
         with torch.cuda.stream(side[1]):
             rays = P.trace_rays(theta, times)
         g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
@@ -337,7 +350,7 @@ def main():
 
     def staged(theta):
         # stage timing: the same calls one after the other on one stream
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         ev[0].record(stream)
         P.solve(theta, times=times, rec_times=rect, records=rec)
         ev[1].record(stream)
@@ -347,8 +360,10 @@ def main():
         ev[3].record(stream)
         P.backward(theta, times, rec, 2.0 * (rect - t_obs))
         ev[4].record(stream)
+        P.solve_check64(theta, times=times, rec_times=rect, records=rec)
+        ev[5].record(stream)
         torch.cuda.synchronize()
-        for k, name in enumerate(["solve", "check64", "rays", "adjoint"]):
+        for k, name in enumerate(["solve", "check64", "rays", "adjoint", "solve_check64"]):
             stage[name] = stage.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
 
     for _ in range(max(args.warmup, 3)):
@@ -435,6 +450,8 @@ def main():
                    "sweep": {1: "lockstep rounds over all fields", 2: "one warp per field",
                              3: "one CTA per field"}[P.options.sweep],
                    "cuda_graph": graph is not None,
+                   "fp64_check": {"fused": "inside the sweep kernel, per field after its sweep",
+                                  "stream": "own kernel on a side stream after the solve"}[args.check],
                    "l2": "inputs larger than L2 (3.6 GB of fields), no flush"},
         "stage_ms": stage, "evaluations_per_node": roof["evaluations_per_node"],
         "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},

@@ -269,6 +269,22 @@ alf_status alf_check64_nodes(alf_plan* plan, const double* region_theta, const v
                              double* check_times, uint8_t* check_records, double* max_rel, int32_t* n_flips,
                              void* stream);
 
+/* alf_solve followed by alf_check64 of the fields it solved, with the records
+ * of the solve: the same outputs, bit for bit, as the two calls in turn.  With
+ * the CTA-per-field sweep (schedule 3) in FP32, without a velocity table,
+ * clusters of one CTA and no kernel timing, the check runs inside the solve
+ * kernel, on each field right after its sweep converges and while the field is
+ * still in L2 (one launch, no second pass over the fields); otherwise the check
+ * is launched after the solve on `stream`.  The check reads the field before
+ * the frozen marks are cleared and takes |tau| of every value, as the
+ * separate check reads the cleared field.
+ *  max_rel    [nfields] double, output, as alf_check64
+ *  n_flips    [nfields] int32, output: nodes whose FP64 record differs from
+ *             the one this solve wrote to `records` (0 when records is NULL)
+ * Other arguments as alf_solve.  Status and errors as alf_solve. */
+alf_status alf_solve_check64(alf_plan* plan, const double* region_theta, void* times, void* rec_times,
+                             uint8_t* records, double* max_rel, int32_t* n_flips, void* stream);
+
 /* Ray tracing (Sec. 5.1) for every (sample, source, receiver): the ray starts
  * at the receiver and walks plane by plane to the source through the source's
  * field (reciprocity), choosing the plane family most perpendicular to the last

@@ -145,6 +145,20 @@ class Plan:
                     C.c_void_p(records.data_ptr()) if records is not None else None, self._stream())
         return times, rec_times
 
+    def solve_check64(self, theta, times=None, rec_times=None, records=None, with_receivers=True):
+        """The solve and the FP64 check of its fields in one call: (times, rec_times, max_rel, flips)."""
+        times = self.new_times() if times is None else times
+        if with_receivers and rec_times is None and self.nrec:
+            rec_times = self.new_rec_times()
+        assert theta.dtype == torch.float64 and theta.is_cuda and theta.is_contiguous()
+        max_rel = torch.empty(self.nfields, dtype=torch.float64, device=self._dev())
+        flips = torch.empty(self.nfields, dtype=torch.int32, device=self._dev())
+        B.alf_solve_check64(self.ctx, self.plan, C.c_void_p(theta.data_ptr()), C.c_void_p(times.data_ptr()),
+                            C.c_void_p(rec_times.data_ptr()) if rec_times is not None else None,
+                            C.c_void_p(records.data_ptr()) if records is not None else None,
+                            C.c_void_p(max_rel.data_ptr()), C.c_void_p(flips.data_ptr()), self._stream())
+        return times, rec_times, max_rel, flips
+
     def check64(self, theta, times, records=None):
         max_rel = torch.empty(self.nfields, dtype=torch.float64, device=self._dev())
         flips = torch.empty(self.nfields, dtype=torch.int32, device=self._dev())

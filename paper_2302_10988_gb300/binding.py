@@ -26,7 +26,8 @@ ALF_INIT_RADIUS, ALF_INIT_HIERARCHY = 0, 1
 EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error", "alf_plan_create",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
            "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats", "alf_plan_autotune",
-           "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient", "alf_check64_nodes")
+           "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient", "alf_check64_nodes",
+           "alf_solve_check64")
 
 
 class AlfError(RuntimeError):
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH):
         L.alf_check64.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.alf_check64_nodes.restype = C.c_int
         L.alf_check64_nodes.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.alf_solve_check64.restype = C.c_int
+        L.alf_solve_check64.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.alf_trace_rays.restype = C.c_int
         L.alf_trace_rays.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.alf_ray_gradient.restype = C.c_int
@@ -181,6 +184,11 @@ def alf_plan_options(plan) -> alf_options:
 
 def alf_solve(ctx, plan, theta_ptr, times_ptr, rec_ptr, records_ptr, stream):
     _check(ctx, load().alf_solve(plan, theta_ptr, times_ptr, rec_ptr, records_ptr, stream))
+
+
+def alf_solve_check64(ctx, plan, theta_ptr, times_ptr, rec_ptr, records_ptr, max_rel_ptr, flips_ptr, stream):
+    _check(ctx, load().alf_solve_check64(plan, theta_ptr, times_ptr, rec_ptr, records_ptr, max_rel_ptr, flips_ptr,
+                                         stream))
 
 
 def alf_check64(ctx, plan, theta_ptr, times_ptr, records_ptr, max_rel_ptr, flips_ptr, stream):

@@ -752,16 +752,22 @@ alf_status alf_plan_options(const alf_plan* p, alf_options* out)
     return ALF_OK;
 }
 
-alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_times, uint8_t* records, void* stream)
+}  // extern "C"
+
+// The forward solve; with max_rel / n_flips also the FP64 check of its fields (alf_solve_check64), fused into
+// the CTA sweep where that kernel can run it, else launched after the solve.
+static alf_status solve_impl(alf_plan* p, const double* theta, void* times, void* rec_times, uint8_t* records,
+                             double* max_rel, int32_t* n_flips, cudaStream_t st)
 {
-    if (!p) return ALF_ERR_INVALID_ARG;
     alf_ctx* ctx = p->ctx;
-    if (!theta || !times) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: null theta or times");
-    if (rec_times && p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: plan has no receivers");
-    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t st = as_stream(stream);
     const int prec = p->opt.precision;
     const int gm = p->opt.group_model;
+    const bool fused = max_rel && p->sweep_mode == 3 && !p->opt.time_kernels &&
+                       fim_cta_can_check(prec, p->opt.velocity_table, p->cta_cluster);
+    if (max_rel) {
+        ALF_CUDA(ctx, launch_prep_regions(ALF_FP64, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm,
+                                          p->d_regions64, st, p->d_vtab64));
+    }
     ALF_CUDA(ctx, launch_prep_regions(prec, p->d_mats, p->d_region_mat, theta, p->d_h, p->B, p->R, gm, p->d_regions, st,
                                       p->d_vtab));
     ALF_CUDA(ctx, launch_fill_inf(prec, times, p->total_nodes, st));
@@ -829,6 +835,14 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     a.q = p->d_q;
     a.records = records;
     a.vtable = p->opt.velocity_table;
+    if (fused) {
+        ALF_CUDA(ctx, cudaMemsetAsync(max_rel, 0, sizeof(double) * p->nfields, st));
+        ALF_CUDA(ctx, cudaMemsetAsync(n_flips, 0, sizeof(int32_t) * p->nfields, st));
+        a.regions64 = p->d_regions64;
+        a.frozen_bits = p->d_frozen;
+        a.max_rel = max_rel;
+        a.n_flips = n_flips;
+    }
     if (p->sweep_mode == 2 || p->sweep_mode == 3) {
         // field-resident sweep: the whole fixed-point iteration in one launch
         const bool timing = p->opt.time_kernels != 0;
@@ -840,7 +854,7 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
         if (p->sweep_mode == 2) ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
         else
             ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, p->cta_threads, p->cta_cluster,
-                                         st));
+                                         st, fused));
         if (timing) {
             ALF_CUDA(ctx, cudaEventRecord(p->ev[1], st));
             ALF_CUDA(ctx, cudaEventSynchronize(p->ev[1]));
@@ -857,7 +871,35 @@ alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_ti
     }
     ALF_CUDA(ctx, launch_finalize(prec, times, p->d_fields, p->nfields, p->box, p->d_rec, p->S, p->Rr, rec_times,
                                   records, st));
+    if (max_rel && !fused)
+        ALF_CUDA(ctx, launch_check64(prec, times, p->d_fields, p->nfields, p->d_map, p->d_regions64, p->R, records,
+                                     p->d_frozen, p->box, max_rel, n_flips, ctx->nsm * ALF_CHECK_CTAS_PER_SM, st,
+                                     p->opt.velocity_table));
     return ALF_OK;
+}
+
+extern "C" {
+
+alf_status alf_solve(alf_plan* p, const double* theta, void* times, void* rec_times, uint8_t* records, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: null theta or times");
+    if (rec_times && p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    return solve_impl(p, theta, times, rec_times, records, nullptr, nullptr, as_stream(stream));
+}
+
+alf_status alf_solve_check64(alf_plan* p, const double* theta, void* times, void* rec_times, uint8_t* records,
+                             double* max_rel, int32_t* n_flips, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!theta || !times || !max_rel || !n_flips)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve_check64: null theta, times, max_rel or n_flips");
+    if (rec_times && p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_solve_check64: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    return solve_impl(p, theta, times, rec_times, records, max_rel, n_flips, as_stream(stream));
 }
 
 alf_status alf_check64(alf_plan* p, const double* theta, const void* times, const uint8_t* records, double* max_rel,

@@ -58,6 +58,11 @@ struct FimLaunch {
     QueueState* q;
     uint8_t* records;
     int vtable;                    // the regions carry velocity tables (kernels compiled with the lookup)
+    // FP64 check fused into the CTA sweep (launch_fim_cta with check): RegionP<double>, frozen bitmaps, outputs
+    const void* regions64 = nullptr;
+    const unsigned* frozen_bits = nullptr;
+    double* max_rel = nullptr;
+    int32_t* n_flips = nullptr;
 };
 
 // kernels (alf_kernels.cu)
@@ -93,7 +98,9 @@ int fim_warp_ctas_per_sm(int precision, unsigned words_per_warp, bool vt);  // 0
 // field-resident sweep by a CTA per field (few large fields); bitmaps of up to smem_words words in shared memory
 // (threads: 64..512 per CTA; cluster: 1, or 2 / 4 / 8 CTAs of 512 threads sharing one field)
 cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           int threads, int cluster, cudaStream_t st);
+                           int threads, int cluster, cudaStream_t st, bool check = false);
+// the CTA sweep can run each field's FP64 check itself (FP32, no velocity table, one CTA per field)
+bool fim_cta_can_check(int precision, int vtable, int cluster);
 int fim_cta_grid(int precision, unsigned smem_words, bool vt, int threads, int cluster, int nsm);  // CTAs; 0: none
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,

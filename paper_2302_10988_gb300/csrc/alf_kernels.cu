@@ -15,6 +15,7 @@
 
 #include "alf_internal.h"
 #include "alf_sweep.cuh"
+#include "alf_check.cuh"
 
 namespace alf {
 
@@ -581,7 +582,9 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 1)
 // Field-resident sweep by a whole CTA (few large fields), or by a cluster of CS CTAs on CS SMs (fewer fields
 // than SMs): the same rounds, barriers between the steps.  The dirty bitmap is in shared memory (rank 0's)
 // when the field's fits, else in the field's global bitmap.  Rank 0 takes the fields from the queue.
-template <typename T, int NT, bool VT, int CS>
+// CHK: once a field is solved, the same CTA runs the FP64 check of every node of it (the field is then still
+// in L1/L2, and its FP64 work overlaps the ALU-bound sweep of the fields on the other CTAs of the SM).
+template <typename T, int NT, bool VT, int CS, bool CHK = false>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
     fim_cta_kernel(FimLaunch a, const unsigned* order, unsigned smem_words)
 {
@@ -633,6 +636,32 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
             atomicMax(&a.q->rounds, (unsigned long long)rounds);
         }
         sweep_sync<CS>();
+        if constexpr (CHK) {
+            // the FP64 check of the field (as check64_kernel): largest relative residual, records that differ
+            const unsigned* fb = a.frozen_bits + (size_t)f * frozen_words(a.box);
+            const RegionP<double>* r64 = (const RegionP<double>*)a.regions64 + (size_t)fd.sample * a.nregions;
+            float mx = 0.f;
+            int flips = 0;
+            for (int me = (int)(rank * NT + threadIdx.x); me < fd.nx * fd.ny; me += NT * CS) {
+                double F;
+                int rec;
+                T tme;
+                if (!check_node<T, VT>(g.tf, fb, a.box, fd, me, r64, g.map, F, rec, tme)) continue;
+                const float res = fabsf((float)(F - (double)tme)) / (float)tme;
+                if (tme > T(0)) mx = fmaxf(mx, res);
+                if (g.rec && g.rec[me] != (uint8_t)rec) flips++;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                flips += __shfl_xor_sync(0xffffffffu, flips, o);
+            }
+            if ((threadIdx.x & 31u) == 0u) {
+                // max of non-negative doubles through their bit patterns
+                if (mx > 0.f)
+                    atomicMax((unsigned long long*)(a.max_rel + f), (unsigned long long)__double_as_longlong((double)mx));
+                if (flips) atomicAdd(a.n_flips + f, flips);
+            }
+        }
     }
 }
 
@@ -640,12 +669,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 512 / NT : 1)
 // warps per field put more fields on an SM at once; more warps finish a large field sooner (512: a whole
 // SM's FP32 register file for one field, for batches with no more fields than SMs).  Clusters of 2, 4 or 8
 // 512-thread CTAs spread one field over as many SMs.
-template <typename T, int NT, bool VT, int CS>
+template <typename T, int NT, bool VT, int CS, bool CHK = false>
 static cudaError_t fim_cta_smem(unsigned smem_words, size_t* smem)
 {
     *smem = (size_t)smem_words * sizeof(unsigned);
     if (*smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fim_cta_kernel<T, NT, VT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(fim_cta_kernel<T, NT, VT, CS, CHK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)*smem);
 }
 
@@ -666,15 +695,15 @@ static cudaLaunchConfig_t cta_config(int grid, int nt, int cs, size_t smem, cuda
     return cfg;
 }
 
-template <typename T, int NT, bool VT, int CS>
+template <typename T, int NT, bool VT, int CS, bool CHK = false>
 static cudaError_t fim_cta_t(const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
                              cudaStream_t st)
 {
     size_t smem = 0;
-    cudaError_t e = fim_cta_smem<T, NT, VT, CS>(smem_words, &smem);
+    cudaError_t e = fim_cta_smem<T, NT, VT, CS, CHK>(smem_words, &smem);
     if (e != cudaSuccess) return e;
     if constexpr (CS == 1) {
-        fim_cta_kernel<T, NT, VT, 1><<<grid, NT, smem, st>>>(a, order, smem_words);
+        fim_cta_kernel<T, NT, VT, 1, CHK><<<grid, NT, smem, st>>>(a, order, smem_words);
         e = cudaGetLastError();
     } else {
         cudaLaunchAttribute attr[1];
@@ -707,9 +736,25 @@ static cudaError_t fim_cta_nt(const FimLaunch& a, const unsigned* order, unsigne
     }
 }
 
-cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
-                           int threads, int cluster, cudaStream_t st)
+bool fim_cta_can_check(int precision, int vtable, int cluster)
 {
+    return precision == ALF_FP32 && !vtable && cluster == 1;
+}
+
+cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                           int threads, int cluster, cudaStream_t st, bool check)
+{
+    if (check) {
+        // the sweep with each field's FP64 check (FP32 fields, run-time Christoffel solve, one CTA per field)
+        if (!fim_cta_can_check(precision, a.vtable, cluster)) return cudaErrorInvalidValue;
+        switch (threads) {
+        case 64: return fim_cta_t<float, 64, false, 1, true>(a, order, smem_words, grid, st);
+        case 128: return fim_cta_t<float, 128, false, 1, true>(a, order, smem_words, grid, st);
+        case 256: return fim_cta_t<float, 256, false, 1, true>(a, order, smem_words, grid, st);
+        case 512: return fim_cta_t<float, 512, false, 1, true>(a, order, smem_words, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (a.vtable)
         return precision == ALF_FP64 ? fim_cta_nt<double, true>(a, order, smem_words, grid, threads, cluster, st)
                                      : fim_cta_nt<float, true>(a, order, smem_words, grid, threads, cluster, st);
@@ -903,63 +948,9 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
 }
 
 // ---------------------------------------------------------------------------
-// check64: F in double precision at every node of a solved field.  Frozen
+// check64: F in double precision at every node of a solved field (alf_check.cuh).  Frozen
 // nodes come from the per-field bitmap of the initialisation box.
 // ---------------------------------------------------------------------------
-ALF_D bool box_frozen(const unsigned* bits, int box, const FieldDesc& fd, int i, int j)
-{
-    const int di = i - fd.si, dj = j - fd.sj;
-    if (di < -box || di > box || dj < -box || dj > box) return false;
-    const int bit = (dj + box) * (2 * box + 1) + (di + box);
-    return (bits[bit >> 5] >> (bit & 31)) & 1u;
-}
-
-// At a fixed point, F at D reads exactly the neighbours that precede D in key
-// order, so the check evaluates in FP64 the update U of that known set.  The
-// FP64 pipe is the bottleneck, so only what needs it runs there: feasibility
-// and the square metrics tau_C - tau_B are exact on the stored times (a
-// difference of two FP32 times within a factor two of each other is exact in
-// FP32; a node with any other feasible square takes the all-FP64 path), the
-// best square is found by exact comparisons, and only its stencil time (the
-// next best's when it is not usable) is evaluated in FP64.  Triangle metrics
-// and the fallback, which need FP64 arithmetic, are evaluated only when no
-// square is usable.  All decisions are the ones an all-FP64 evaluation makes.
-template <typename T, bool VT>
-ALF_D double check_pair_time(int bp, const T (&t)[12], const RegionP<double>& R, int& rec)
-{
-    // the pair's geometry as FP64 constants chosen by predicated moves (no integer-to-FP64 conversion, which
-    // runs on the slow FP64 pipe); dxC, dyC: C - A
-    double xA = 0.0, yA = 0.0, xB = 0.0, yB = 0.0, dxC = 0.0, dyC = 0.0;
-    int r = 255;
-    T tA = T(0), tB = T(0), tC = T(0);
-#pragma unroll
-    for (int p = 0; p < 16; ++p)
-        if (p == bp) {
-            const bool m1 = t[pp(p)] <= t[pq(p)];
-            xA = double(sdi(pa(p)));
-            yA = double(sdj(pa(p)));
-            xB = m1 ? double(sdi(pp(p))) : double(sdi(pq(p)));
-            yB = m1 ? double(sdj(pp(p))) : double(sdj(pq(p)));
-            dxC = m1 ? double(sdi(pq(p)) - sdi(pa(p))) : double(sdi(pp(p)) - sdi(pa(p)));
-            dyC = m1 ? double(sdj(pq(p)) - sdj(pa(p))) : double(sdj(pp(p)) - sdj(pa(p)));
-            tA = t[pa(p)];
-            tB = m1 ? t[pp(p)] : t[pq(p)];
-            tC = m1 ? t[pq(p)] : t[pp(p)];
-            r = 2 * p + (m1 ? 0 : 1);
-        }
-    // the stencil time with its geometry scaled by den = tau_C - tau_A (> 0 for a feasible pair): the
-    // cross product scales by den and the phase term by den^2, so tau_D needs no division, and one
-    // reciprocal square root instead of a square root and two divisions.  The differences of FP32
-    // times are exact in FP64.
-    const double num = (double)tB - (double)tA, den = (double)tC - (double)tA;
-    const double Ex = xA * den + num * dxC, Ey = yA * den + num * dyC;
-    const double ux = xB * den - Ex, uy = yB * den - Ey;
-    const double cross = fabs(yB * Ex - xB * Ey);
-    const double v = (double)tB + R.h * cross * rsqrt(phase_L<double, VT>(R, ux, uy));
-    rec = r;
-    return v > (double)tC ? v : alf_inf<double>();
-}
-
 template <typename T, bool VT>
 __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint32_t* region_map,
                                const RegionP<double>* regions, int nregions, const uint8_t* records,
@@ -971,7 +962,6 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
     constexpr int CH = 32;  // chunks per field
     __shared__ float s_max[256];
     __shared__ int s_flip[256];
-    const double inf64 = alf_inf<double>();
     for (long long w = blockIdx.x; w < (long long)nfields * CH; w += gridDim.x) {
     const int f = (int)(w / CH), chunk = (int)(w % CH);
     const FieldDesc fd = fields[f];
@@ -981,112 +971,15 @@ __global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfie
     int flips = 0;
     const T* tf = times + fd.node_off;
     for (int me = chunk * blockDim.x + threadIdx.x; me < n; me += CH * blockDim.x) {
-        const int i = me % fd.nx, j = me / fd.nx;
-        const T tme = abs_(tf[me]);
-        // frozen nodes and nodes without a value keep their time (records 254 / 255)
-        const bool fz = box_frozen(fb, box, fd, i, j);
-        if (fz || !(tme < alf_inf<T>())) {
-            if (F_out) F_out[fd.node_off + me] = (double)tme;
-            if (rec_out) rec_out[fd.node_off + me] = fz ? 254 : 255;
+        double F;
+        int rec;
+        T tme;
+        const bool checked = check_node<T, VT>(tf, fb, box, fd, me, regions + (size_t)fd.sample * nregions,
+                                               region_map + fd.map_off, F, rec, tme);
+        if (!checked) {
+            if (F_out) F_out[fd.node_off + me] = F;
+            if (rec_out) rec_out[fd.node_off + me] = (uint8_t)rec;
             continue;
-        }
-        T t[12];
-        unsigned known = 0u;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int ii = i + sdi(k), jj = j + sdj(k);
-            t[k] = alf_inf<T>();
-            if (ii < 0 || jj < 0 || ii >= fd.nx || jj >= fd.ny) continue;
-            const T v = abs_(tf[(long long)jj * fd.nx + ii]);
-            t[k] = v;
-            const bool before = sord(k) < 12 ? v <= tme : v < tme;
-            if (box_frozen(fb, box, fd, ii, jj) || before) known |= 1u << k;
-        }
-        const RegionP<double> R = regions[(size_t)fd.sample * nregions + region_map[fd.map_off + me]];
-        // feasible pairs (exact comparisons) and the square metrics
-        unsigned feas = 0u;
-        bool exact = true;
-        T msq[8];
-#pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            const T tA = t[pa(p)], tP = t[pp(p)], tQ = t[pq(p)];
-            const bool ok = ((known >> pa(p)) & (known >> pp(p)) & (known >> pq(p)) & 1u) && tA < tP && tA < tQ;
-            if (ok) feas |= 1u << p;
-            if (p < 8) {
-                const T lo = tP <= tQ ? tP : tQ, hi = tP <= tQ ? tQ : tP;
-                msq[p] = hi - lo;
-                if (ok && !(hi <= T(2) * lo)) exact = false;
-            }
-        }
-        double F = inf64;
-        int rec = 255;
-        // squares: best metric first, the next best when a pair is not usable
-        unsigned cand = feas & 0xFFu;
-#pragma unroll 1
-        for (int tries = 0; tries < 8 && cand; ++tries) {
-            int bp = -1;
-            if (exact) {
-                T bm = alf_inf<T>();
-#pragma unroll
-                for (int p = 0; p < 8; ++p)
-                    if (((cand >> p) & 1u) && (bp < 0 || msq[p] < bm)) {
-                        bm = msq[p];
-                        bp = p;
-                    }
-            } else {
-                double bm = inf64;
-#pragma unroll
-                for (int p = 0; p < 8; ++p) {
-                    const double mp = fabs((double)t[pq(p)] - (double)t[pp(p)]);
-                    if (((cand >> p) & 1u) && (bp < 0 || mp < bm)) {
-                        bm = mp;
-                        bp = p;
-                    }
-                }
-            }
-            cand &= ~(1u << bp);
-            int r;
-            const double v = check_pair_time<T, VT>(bp, t, R, r);
-            if (v < inf64) {
-                F = v;
-                rec = r;
-                break;
-            }
-        }
-        // triangles (FP64 metrics), only when no square is usable
-        cand = rec == 255 ? (feas & 0xFF00u) : 0u;
-#pragma unroll 1
-        for (int tries = 0; tries < 8 && cand; ++tries) {
-            int bp = -1;
-            double bm = inf64;
-#pragma unroll
-            for (int p = 8; p < 16; ++p) {
-                const double mp = fabs((double)t[pq(p)] - ((1.4142135623730951 - 1.0) * (double)t[pa(p)] +
-                                                           (2.0 - 1.4142135623730951) * (double)t[pp(p)]));
-                if (((cand >> p) & 1u) && (bp < 0 || mp < bm)) {
-                    bm = mp;
-                    bp = p;
-                }
-            }
-            cand &= ~(1u << bp);
-            int r;
-            const double v = check_pair_time<T, VT>(bp, t, R, r);
-            if (v < inf64) {
-                F = v;
-                rec = r;
-                break;
-            }
-        }
-        if (rec == 255) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                if (!((known >> k) & 1u)) continue;
-                const double g = (double)t[k] + ((k >= 8) ? 2.0 * R.fb[scls(k)] : R.fb[scls(k)]);
-                if (g < F) {
-                    F = g;
-                    rec = 32 + k;
-                }
-            }
         }
         // relative residual: the difference in FP64, its ratio in FP32
         const float res = fabsf((float)(F - (double)tme)) / (float)tme;

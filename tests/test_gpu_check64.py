@@ -91,3 +91,27 @@ def test_check64_corner_sources_and_no_box(api, oracle):
     wl.samples[0].src[:] = [[0, 0], [89, 89], [0, 45], [44, 44]]
     for r0 in (0, 5):
         _compare(api, oracle, wl, "fp32", range(4), r0=r0)
+
+
+@pytest.mark.parametrize("precision,sweep,threads", [("fp32", 3, 0), ("fp32", 3, 64), ("fp32", 3, 512),
+                                                     ("fp32", 1, 0), ("fp32", 2, 0), ("fp64", 3, 0),
+                                                     ("fp64", 2, 0)])
+def test_solve_check64_equals_solve_then_check(api, precision, sweep, threads):
+    """alf_solve_check64 (the check inside the CTA sweep kernel where that kernel runs it, else launched after
+    the solve) returns the fields, records and check summaries of alf_solve followed by alf_check64, bit for
+    bit, on an uneven batch (several CTA tiles per field, ragged tails), with and without records."""
+    wl = W.weld_batch(nsamples=4, nsrc=3, nrec=4, sizes=(64, 96, 160))
+    P = api.Plan(wl, precision=precision, sweep=sweep, cta_threads=threads)
+    th = P.theta_tensor()
+    rec1, rec2 = P.new_records(), P.new_records()
+    t1, rt1 = P.solve(th, records=rec1)
+    mr1, fl1 = P.check64(th, t1, rec1)
+    t2, rt2, mr2, fl2 = P.solve_check64(th, records=rec2)
+    _, _, mr3, fl3 = P.solve_check64(th)
+    assert P.status() == 0
+    assert torch.equal(t1, t2) and torch.equal(rt1, rt2) and torch.equal(rec1, rec2)
+    assert torch.equal(mr1, mr2) and torch.equal(fl1, fl2)
+    assert torch.equal(mr1, mr3) and int(fl3.abs().sum()) == 0
+    assert float(mr1.max()) < (1e-6 if precision == "fp32" else 1e-12)
+    if precision == "fp32" and sweep == 3:
+        assert int(fl1.sum()) > 0 or float(mr1.max()) > 0.0  # the summaries were written, not left zero
