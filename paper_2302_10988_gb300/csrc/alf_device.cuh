@@ -181,20 +181,46 @@ ALF_HD constexpr int pq(int p) { constexpr int t[16] = {0, 0, 3, 2, 6, 6, 4, 5, 
 // the middle time tB = min(tP, tQ) is the paper's wavefront EB (E on AC at time tB, C the later of P, Q), with
 // normal g; D lies |tau_lin(D) - tB| / |g| from it, tau_lin(D) = tA - g.A the plane's time at D.  So
 //   tau_D = tB + h |tau_lin(D) - tB| / (|g| v(g / |g|)) = tB + h |tau_lin(D) - tB| / sqrt(|g|^2 lambda(g) / rho),
-// the same time as the paper's construction, with no division: the inverse of (P - A, Q - A) is a constant of
-// the stencil (its determinant is +-1 or +-2), folded at compile time once p is.
-template <typename T, bool VT = false>
-ALF_D T pair_time(int p, T tA, T tP, T tQ, const RegionP<T>& R)
+// the same time as the paper's construction, with no division.  The inverse of (P - A, Q - A) is a constant of
+// the stencil: its determinant is +-1 or +-2, so g = (c1 dP + c2 dQ, c3 dP + c4 dQ) with every c in
+// {0, +-1/2, +-1}, and A's offsets are in {-2, ..., 2}.  The pair's geometry travels as one word of six
+// three-bit codes (2 c + 2 and offset + 2), so that the pair can be chosen at run time; every product with
+// these constants is exact, so the time does not depend on how the constants arrive.
+ALF_HD constexpr unsigned pair_geom(int p)
 {
     const int xa = sdi(pa(p)), ya = sdj(pa(p));
     const int e1x = sdi(pp(p)) - xa, e1y = sdj(pp(p)) - ya;
     const int e2x = sdi(pq(p)) - xa, e2y = sdj(pq(p)) - ya;
-    const T inv = T(1) / T(e1x * e2y - e1y * e2x);
+    const int det = e1x * e2y - e1y * e2x;
+    const int c[6] = {2 * e2y / det + 2, -2 * e1y / det + 2, -2 * e2x / det + 2, 2 * e1x / det + 2, xa + 2, ya + 2};
+    unsigned w = 0u;
+    for (int k = 0; k < 6; ++k) w |= (unsigned)c[k] << (3 * k);
+    return w;
+}
+
+// code k of a geometry word as (code - 2) * scale, scale 1/2 or 1.  FP32: the code is placed in the low bits of
+// 1.5 * 2^23 (whose ulp is 1), so the float equals 12582912 + code exactly and one FMA gives the value, exactly,
+// with no integer-to-float conversion.
+template <typename T>
+ALF_D T geom_code(unsigned w, int k, T scale)
+{
+    return T((int)((w >> (3 * k)) & 7u) - 2) * scale;
+}
+template <>
+ALF_D float geom_code<float>(unsigned w, int k, float scale)
+{
+    const float b = __uint_as_float(((w >> (3 * k)) & 7u) | 0x4B400000u);
+    return fmaf(b, scale, -12582914.0f * scale);
+}
+
+template <typename T, bool VT = false>
+ALF_D T pair_time_geom(unsigned geom, T tA, T tP, T tQ, const RegionP<T>& R)
+{
     const T dP = tP - tA, dQ = tQ - tA;
-    const T gx = (T(e2y) * dP - T(e1y) * dQ) * inv;
-    const T gy = (T(e1x) * dQ - T(e2x) * dP) * inv;
+    const T gx = geom_code<T>(geom, 0, T(0.5)) * dP + geom_code<T>(geom, 1, T(0.5)) * dQ;
+    const T gy = geom_code<T>(geom, 2, T(0.5)) * dP + geom_code<T>(geom, 3, T(0.5)) * dQ;
     const T tB = tP < tQ ? tP : tQ;
-    const T lin = tA - (T(xa) * gx + T(ya) * gy);
+    const T lin = tA - (geom_code<T>(geom, 4, T(1)) * gx + geom_code<T>(geom, 5, T(1)) * gy);
     // phase_L takes the wavefront direction u, whose normal (-u_y, u_x) is g
     return tB + R.h * abs_(lin - tB) * rsqrt_(phase_L<T, VT>(R, gy, -gx));
 }
@@ -312,30 +338,27 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
 #pragma unroll
     for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? rk[k] : (((fz >> k) & 1u) ? -1 : 64);
     const int nc = __popc(cd);
-    // pairs: metric (+inf when not usable), time, availability step; ev_*: bit (step + 1)
-    T pm[16], pv[16];
+    // pairs: metric (+inf when not feasible) and availability step; ev_*: bit (step + 1) of a feasible pair.
+    // A feasible pair is usable when its time is later than C; that time is evaluated only when the walk
+    // chooses the pair (a pair found not usable is set aside and the choice made again), so that one or two
+    // stencil times are evaluated per node instead of one per feasible pair.
+    T pm[16];
     int rp[16];
-    unsigned prow_m2 = 0u, ev_sq = 0u, ev_tr = 0u;  // prow_m2 bit p: member 2 (tau_P > tau_Q)
+    unsigned ev_sq = 0u, ev_tr = 0u;
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         constexpr T k1 = T(1.4142135623730951) - T(1.0);
         constexpr T k2 = T(2.0) - T(1.4142135623730951);
         const int A = pa(p), P = pp(p), Q = pq(p);
         const T tA = t[A], tP = t[P], tQ = t[Q];
-        const bool m1 = tP <= tQ;
-        if (!m1) prow_m2 |= 1u << p;
         rp[p] = max(rk[A], max(rk[P], rk[Q]));
         pm[p] = inf;
-        pv[p] = inf;
         if (rp[p] < 64 && tA < tP && tA < tQ) {
+            const bool m1 = tP <= tQ;
             const T tB = m1 ? tP : tQ, tC = m1 ? tQ : tP;
-            const T v = pair_time<T, VT>(p, tA, tP, tQ, R);
-            if (v > tC) {
-                pv[p] = v;
-                pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));
-                if (p < 8) ev_sq |= 1u << (rp[p] + 1);
-                else ev_tr |= 1u << (rp[p] + 1);
-            }
+            pm[p] = (p < 8) ? (tC - tB) : abs_(tQ - (k1 * tA + k2 * tP));
+            if (p < 8) ev_sq |= 1u << (rp[p] + 1);
+            else ev_tr |= 1u << (rp[p] + 1);
         }
     }
     // straight-ray fallback values of the slots
@@ -356,10 +379,8 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         if (ev_pair > 1u) {  // the first pair is not available from the start
             T gmin = inf;
 #pragma unroll
-            for (int q = 0; q < 12; ++q) {
-                const T gq = t[q] + ((q >= 8) ? T(2) * R.fb[scls(q)] : R.fb[scls(q)]);
-                if (rk[q] < 64 && gq < gmin) gmin = gq;
-            }
+            for (int q = 0; q < 12; ++q)
+                if (rk[q] < 64 && g[q] < gmin) gmin = g[q];
             int cmin = 0;
 #pragma unroll
             for (int q = 0; q < 12; ++q)
@@ -368,29 +389,51 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
             if (cmin - 1 >= first) k = first;
         }
     }
+    unsigned unusable = 0u;  // feasible pairs whose time is not later than C
+    int last_p = -1;         // the last pair evaluated and its time
+    T last_v = inf;
 #pragma unroll 1
-    for (int guard = 0; guard < 14; ++guard) {
-        T bm = inf, bv = inf;
-        int br = 255, cls = 0;
+    for (int guard = 0; guard < 32; ++guard) {
+        // the available, possibly usable pair of least metric: squares, else triangles (ties to the lower row)
+        T bm = inf, sA = inf, sP = inf, sQ = inf;
+        int bp = -1;
+        unsigned geom = 0u;
 #pragma unroll
         for (int p = 0; p < 8; ++p)
-            if (rp[p] <= k && pm[p] < bm) {
+            if (rp[p] <= k && !((unusable >> p) & 1u) && pm[p] < bm) {
                 bm = pm[p];
-                bv = pv[p];
-                br = 2 * p + ((prow_m2 >> p) & 1u);
+                bp = p;
+                sA = t[pa(p)];
+                sP = t[pp(p)];
+                sQ = t[pq(p)];
+                geom = pair_geom(p);
             }
-        if (br == 255) {
-            cls = 1;
+        if (bp < 0) {
 #pragma unroll
             for (int p = 8; p < 16; ++p)
-                if (rp[p] <= k && pm[p] < bm) {
+                if (rp[p] <= k && !((unusable >> p) & 1u) && pm[p] < bm) {
                     bm = pm[p];
-                    bv = pv[p];
-                    br = 2 * p + ((prow_m2 >> p) & 1u);
+                    bp = p;
+                    sA = t[pa(p)];
+                    sP = t[pp(p)];
+                    sQ = t[pq(p)];
+                    geom = pair_geom(p);
                 }
         }
-        if (br == 255) {
-            cls = 2;
+        T bv = inf;
+        int br = 255, cls = 2;
+        if (bp >= 0) {
+            const T v = bp == last_p ? last_v : pair_time_geom<T, VT>(geom, sA, sP, sQ, R);
+            if (!(v > (sP <= sQ ? sQ : sP))) {
+                unusable |= 1u << bp;
+                continue;
+            }
+            last_p = bp;
+            last_v = v;
+            bv = v;
+            br = 2 * bp + (sP <= sQ ? 0 : 1);
+            cls = bp < 8 ? 0 : 1;
+        } else {
 #pragma unroll
             for (int q = 0; q < 12; ++q)
                 if (rk[q] <= k && g[q] < bv) {
