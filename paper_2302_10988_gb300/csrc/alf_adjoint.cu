@@ -13,10 +13,12 @@
 //             fallback and the frozen nodes) and the in-degree of every
 //             node (how many later nodes use it);
 //   (everything the sweep touches per node -- weights, lambda, its
-//   contribution lambda * dtau/dtheta, in-degree -- sits in one 32-byte
-//   record (64 bytes in FP64), one DRAM sector per node visit; a user's
-//   contribution and its release of a support node are one vector atomic
-//   on the adjacent (lambda, in-degree) pair in FP32);
+//   contribution lambda * dtau/dtheta, in-degree, its stencil record and
+//   whether it is frozen -- sits in one 32-byte record (64 bytes in FP64):
+//   the release that makes a node ready brings that sector into L2, where
+//   the node's processing then finds all of it; a user's contribution and
+//   its release of a support node are one vector atomic on the adjacent
+//   (lambda, in-degree) pair in FP32);
 //   seed      lambda = dL/dT at the receivers;
 //   rounds    Kahn's order: a node whose users have all been processed is
 //             final; it adds lambda * weight to the nodes it used and releases
@@ -42,7 +44,7 @@ struct alignas(8 * sizeof(T)) AdjNode {
     T lam;            // dL / d tau_D
     T indeg;          // later nodes that use this one, not yet processed (a small integer, exact in T)
     T gn;             // lam * wt (the node's contribution to its region's gradient)
-    T pad;
+    T code;           // the node's stencil record, + 256 when frozen (so that the sweep reads one sector a node)
 };
 static_assert(sizeof(AdjNode<float>) == 32 && sizeof(AdjNode<double>) == 64, "one or two DRAM sectors per node");
 
@@ -168,7 +170,8 @@ __global__ void adj_weights_kernel(AdjLaunch a)
         for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
             const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
             T w0 = T(0), w1 = T(0), w2 = T(0), wt = T(0);
-            if (frozen_at(fb, a.box, fd, i, j)) {
+            const bool fz = frozen_at(fb, a.box, fd, i, j);
+            if (fz) {
                 // straight-ray time from the source: derivative by the source orientation
                 if (i != fd.si || j != fd.sj) {
                     const int rs = a.region_map[fd.map_off + (long long)fd.sj * nx + fd.si];
@@ -213,6 +216,7 @@ __global__ void adj_weights_kernel(AdjLaunch a)
             r.w[1] = w1;
             r.w[2] = w2;
             r.wt = wt;
+            r.code = fz ? T(256) : T(a.records[fd.node_off + n]);
         }
     }
 }
@@ -333,8 +337,12 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
 // Kahn rounds of one field by one warp, fields taken from a queue (largest first).  Only the owning
 // warp touches a field's node records, and the warp barrier at the end of a round orders a round's
 // contributions before the next round reads them (through L2: __ldcg).  With few regions the
-// warp sums the region gradients in shared memory as it goes.
-#define ADJ_U 4  // frontier entries per lane per pass of the field-resident adjoint
+// warp sums the region gradients in shared memory as it goes.  The sweep is a chain of rounds as long as
+// the DAG is deep (thousands on a field of 10^5 nodes), so the latency of a round is the cost: the
+// frontier lists stay in shared memory up to ADJ_CAP entries (beyond that, in the field's global lists),
+// and a node's whole state is one sector already in L2.
+#define ADJ_U 4      // frontier entries per lane per pass of the field-resident adjoint
+#define ADJ_CAP 256  // frontier entries a warp keeps in shared memory per list
 
 template <typename T>
 __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad, int smem_regions)
@@ -344,6 +352,8 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
     double* acc = s_acc + (size_t)(threadIdx.x >> 5) * (smem_regions ? a.nregions : 0);
+    unsigned* const s_lists = (unsigned*)(s_acc + (size_t)(blockDim.x >> 5) * (smem_regions ? a.nregions : 0)) +
+                              (size_t)(threadIdx.x >> 5) * 2 * ADJ_CAP;
     AdjNode<T>* const A = (AdjNode<T>*)a.nodes;
     if (smem_regions)
         for (int r = (int)lane; r < a.nregions; r += 32) acc[r] = 0.0;
@@ -357,17 +367,20 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
         const FieldDesc fd = a.fields[f];
         const int nx = fd.nx, ny = fd.ny;
         AdjNode<T>* const An = A + fd.node_off;
-        const unsigned* fbits = a.frozen_bits + (size_t)f * frozen_words(a.box);
         const uint32_t* map = a.region_map + fd.map_off;
         const int rsrc = map[(long long)fd.sj * nx + fd.si];
         unsigned* const list0 = a.list[0] + fd.node_off;
         unsigned* const list1 = a.list[1] + fd.node_off;
         unsigned nact = a.cnt[f], par = 0u;
         unsigned processed = 0u;  // Kahn's order reaches every node of a DAG exactly once
+        bool first = true;        // the first frontier is all in the global list 0
         while (nact != 0u) {
             processed += nact;
+            // entry e of a list: shared memory below ADJ_CAP (after the first round), else the global list
             const unsigned* LA = par ? list1 : list0;
             unsigned* LB = par ? list0 : list1;
+            const unsigned* SA = s_lists + (par ? ADJ_CAP : 0u);
+            unsigned* SB = s_lists + (par ? 0u : ADJ_CAP);
             unsigned nc = 0u;
             // up to ADJ_U entries per lane at once: their loads, then their releases, are independent, so a
             // round costs about one chain of memory round trips instead of one per 32 entries
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
 #pragma unroll
                 for (int u = 0; u < ADJ_U; ++u) {
                     const unsigned e = base + 32u * u + lane;
-                    nn[u] = e < nact ? LA[e] : ~0u;
+                    nn[u] = e < nact ? ((first || e >= ADJ_CAP) ? LA[e] : SA[e]) : ~0u;
                 }
 #pragma unroll
                 for (int u = 0; u < ADJ_U; ++u) {
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
                         w[u][1] = r.w[1];
                         w[u][2] = r.w[2];
                         g[u] = l[u] * r.wt;
-                        rec[u] = a.records[fd.node_off + nn[u]];
+                        rec[u] = (int)r.code;
                     }
                 }
 #pragma unroll
@@ -402,7 +415,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
                     if (nn[u] == ~0u) continue;
                     const unsigned n = nn[u];
                     const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                    const bool fz = frozen_at(fbits, a.box, fd, i, j);
+                    const bool fz = rec[u] >= 256;
                     if (smem_regions) {
                         if (g[u] != T(0)) atomicAdd(acc + (fz ? rsrc : (int)map[n]), (double)g[u]);
                     } else {
@@ -420,13 +433,18 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const unsigned b = __ballot_sync(FULL, fresh[u][k]);
-                        if (fresh[u][k]) LB[nc + __popc(b & below)] = ms[u][k];
+                        if (fresh[u][k]) {
+                            const unsigned idx = nc + __popc(b & below);
+                            if (idx < ADJ_CAP) SB[idx] = ms[u][k];
+                            else LB[idx] = ms[u][k];
+                        }
                         nc += __popc(b);
                     }
             }
             __syncwarp();
             nact = nc;
             par ^= 1u;
+            first = false;
         }
         // a node left unreleased sits on a cycle: the records do not describe one causal solve
         if (lane == 0 && processed != (unsigned)(nx * ny)) adj_set_error(a.q, ALF_ERR_INCONSISTENT_RECORDS);
@@ -500,7 +518,8 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
         if ((e = cudaMemsetAsync(a.head, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
         adj_frontier_flat_kernel<T><<<fgrid, 256, 0, st>>>(a);
         const int smem_regions = a.nregions <= 512 ? 1 : 0;
-        const size_t smem = smem_regions ? (size_t)8 * a.nregions * sizeof(double) : 0;
+        const size_t smem = (smem_regions ? (size_t)8 * a.nregions * sizeof(double) : 0) +
+                            (size_t)8 * 2 * ADJ_CAP * sizeof(unsigned);
         adj_warp_kernel<T><<<a.warp_grid, 256, smem, st>>>(a, grad, smem_regions);
         note_launches(2);
         if (!smem_regions) {
