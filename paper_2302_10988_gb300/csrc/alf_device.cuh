@@ -270,6 +270,38 @@ ALF_HD int pair_q(int p)
     return (int)((t >> (4 * p)) & 15ull);
 }
 
+// One comparison of the rank counts of the local operator: when a precedes b (a <= b with le, else a < b),
+// add d to w (both counters in one word), or add dm to wm and take dk from wk -- predicated adds, with no
+// select.
+ALF_D void rank_count(unsigned& w, float a, float b, bool le, unsigned d)
+{
+    if (le) asm("{\n\t.reg .pred p;\n\tsetp.le.f32 p, %1, %2;\n\t@p add.u32 %0, %0, %3;\n\t}" : "+r"(w) : "f"(a), "f"(b), "r"(d));
+    else asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %1, %2;\n\t@p add.u32 %0, %0, %3;\n\t}" : "+r"(w) : "f"(a), "f"(b), "r"(d));
+}
+ALF_D void rank_count(unsigned& wm, unsigned& wk, float a, float b, bool le, unsigned dm, unsigned dk)
+{
+    if (le)
+        asm("{\n\t.reg .pred p;\n\tsetp.le.f32 p, %2, %3;\n\t@p add.u32 %0, %0, %4;\n\t@p sub.u32 %1, %1, %5;\n\t}"
+            : "+r"(wm), "+r"(wk) : "f"(a), "f"(b), "r"(dm), "r"(dk));
+    else
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %2, %3;\n\t@p add.u32 %0, %0, %4;\n\t@p sub.u32 %1, %1, %5;\n\t}"
+            : "+r"(wm), "+r"(wk) : "f"(a), "f"(b), "r"(dm), "r"(dk));
+}
+ALF_D void rank_count(unsigned& w, double a, double b, bool le, unsigned d)
+{
+    if (le) asm("{\n\t.reg .pred p;\n\tsetp.le.f64 p, %1, %2;\n\t@p add.u32 %0, %0, %3;\n\t}" : "+r"(w) : "d"(a), "d"(b), "r"(d));
+    else asm("{\n\t.reg .pred p;\n\tsetp.lt.f64 p, %1, %2;\n\t@p add.u32 %0, %0, %3;\n\t}" : "+r"(w) : "d"(a), "d"(b), "r"(d));
+}
+ALF_D void rank_count(unsigned& wm, unsigned& wk, double a, double b, bool le, unsigned dm, unsigned dk)
+{
+    if (le)
+        asm("{\n\t.reg .pred p;\n\tsetp.le.f64 p, %2, %3;\n\t@p add.u32 %0, %0, %4;\n\t@p sub.u32 %1, %1, %5;\n\t}"
+            : "+r"(wm), "+r"(wk) : "d"(a), "d"(b), "r"(dm), "r"(dk));
+    else
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f64 p, %2, %3;\n\t@p add.u32 %0, %0, %4;\n\t@p sub.u32 %1, %1, %5;\n\t}"
+            : "+r"(wm), "+r"(wk) : "d"(a), "d"(b), "r"(dm), "r"(dk));
+}
+
 // ---------------------------------------------------------------------------
 // The local operator F at node D (linear index `me`; the tie order of equal
 // times is the linear index, which for diamond neighbours is the static order
@@ -318,12 +350,18 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
     // are then given rank -1 (frozen: known from the start) or 64 (unknown: never known).
     // (The pair loop runs over the full 12 x 12 square so that it unrolls completely and
     // the arrays stay in registers.)
+    // The 12 counts are bytes of three words, biased by 64 so that no byte ever borrows or carries: byte k
+    // starts at 64 + (11 - k) (as if every later slot preceded it) and each of the 66 comparisons, when k
+    // precedes m, adds one to byte m and takes one from byte k -- one predicated add per word it touches.
     T kt[12];
-    int rk[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        kt[k] = ((cd >> k) & 1u) ? t[k] : inf;
-        rk[k] = 0;
+    for (int k = 0; k < 12; ++k) kt[k] = ((cd >> k) & 1u) ? t[k] : inf;
+    unsigned W[3];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+        W[w] = 0u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) W[w] |= (unsigned)(64 + 11 - (4 * w + b)) << (8 * b);
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k)
@@ -331,12 +369,16 @@ ALF_D T local_F(const T* nb, int me, int nx, const RegionP<T>& R, int& rec)
         for (int m = 0; m < 12; ++m) {
             if (m <= k) continue;
             // key(k) < key(m); on equal times the static order decides
-            const bool lt = sord(k) < sord(m) ? kt[k] <= kt[m] : kt[k] < kt[m];
-            rk[m] += lt ? 1 : 0;
-            rk[k] += lt ? 0 : 1;
+            const unsigned im = 1u << (8 * (m & 3)), ik = 1u << (8 * (k & 3));
+            if ((m >> 2) == (k >> 2)) rank_count(W[m >> 2], kt[k], kt[m], sord(k) < sord(m), im - ik);
+            else rank_count(W[m >> 2], W[k >> 2], kt[k], kt[m], sord(k) < sord(m), im, ik);
         }
+    int rk[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) rk[k] = ((cd >> k) & 1u) ? rk[k] : (((fz >> k) & 1u) ? -1 : 64);
+    for (int k = 0; k < 12; ++k) {
+        const int c = (int)((W[k >> 2] >> (8 * (k & 3))) & 0xFFu) - 64;
+        rk[k] = ((cd >> k) & 1u) ? c : (((fz >> k) & 1u) ? -1 : 64);
+    }
     const int nc = __popc(cd);
     // pairs: metric (+inf when not feasible) and availability step; ev_*: bit (step + 1) of a feasible pair.
     // A feasible pair is usable when its time is later than C; that time is evaluated only when the walk
