@@ -44,8 +44,20 @@ struct alignas(8 * sizeof(T)) AdjNode {
     T lam;            // dL / d tau_D
     T indeg;          // later nodes that use this one, not yet processed (a small integer, exact in T)
     T gn;             // lam * wt (the node's contribution to its region's gradient)
-    T code;           // the node's stencil record, + 256 when frozen (so that the sweep reads one sector a node)
+    T code;           // what the sweep needs of the node's formula, packed (adj_code): one sector a node visit
 };
+
+// The sweep's view of a node's formula, packed into 24 bits (exact in FP32): its support nodes as diamond
+// slots (bits 0-11, four bits each, in the order of the weights), how many it releases (bits 12-13: 3 for a
+// stencil, 1 for the fallback, 0 for a frozen node or a formula with a support point outside the grid),
+// whether it is frozen (bit 14) and the region its contribution goes to (bits 15-23, when the regions are
+// few enough for the sweep to sum them in shared memory: the node's own, a frozen node's source's).
+#define ADJ_SMEM_REGIONS 512
+ALF_HD unsigned adj_code(const int s[3], int ns, bool frozen, int region)
+{
+    return (unsigned)s[0] | ((unsigned)s[1] << 4) | ((unsigned)s[2] << 8) | ((unsigned)ns << 12) |
+           (frozen ? 1u << 14 : 0u) | ((unsigned)(region & (ADJ_SMEM_REGIONS - 1)) << 15);
+}
 static_assert(sizeof(AdjNode<float>) == 32 && sizeof(AdjNode<double>) == 64, "one or two DRAM sectors per node");
 
 // A processed user hands its contribution to a support node and releases it: lam += c, indeg -= 1; returns
@@ -211,12 +223,22 @@ __global__ void adj_weights_kernel(AdjLaunch a)
                 for (int k = 0; k < 3; ++k)
                     if (k < ns) atomicAdd(&An[ms[k]].indeg, T(1));
             }
+            int s[3] = {0, 0, 0}, ns = 0, region = 0;
+            if (fz) {
+                region = a.region_map[fd.map_off + (long long)fd.sj * nx + fd.si];
+            } else {
+                const int rec = a.records[fd.node_off + n];
+                unsigned ms[3];
+                ns = support_nodes(rec, i, j, nx, ny, ms);
+                support_slots(rec, s);
+                region = a.region_map[fd.map_off + n];
+            }
             AdjNode<T>& r = An[n];
             r.w[0] = w0;
             r.w[1] = w1;
             r.w[2] = w2;
             r.wt = wt;
-            r.code = fz ? T(256) : T(a.records[fd.node_off + n]);
+            r.code = T(adj_code(s, ns, fz, a.nregions <= ADJ_SMEM_REGIONS ? region : 0));
         }
     }
 }
@@ -367,8 +389,6 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
         const FieldDesc fd = a.fields[f];
         const int nx = fd.nx, ny = fd.ny;
         AdjNode<T>* const An = A + fd.node_off;
-        const uint32_t* map = a.region_map + fd.map_off;
-        const int rsrc = map[(long long)fd.sj * nx + fd.si];
         unsigned* const list0 = a.list[0] + fd.node_off;
         unsigned* const list1 = a.list[1] + fd.node_off;
         unsigned nact = a.cnt[f], par = 0u;
@@ -413,19 +433,19 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad
                     fresh[u][0] = fresh[u][1] = fresh[u][2] = false;
                     ms[u][0] = ms[u][1] = ms[u][2] = 0u;
                     if (nn[u] == ~0u) continue;
-                    const unsigned n = nn[u];
-                    const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
-                    const bool fz = rec[u] >= 256;
+                    const unsigned n = nn[u], code = (unsigned)rec[u];
                     if (smem_regions) {
-                        if (g[u] != T(0)) atomicAdd(acc + (fz ? rsrc : (int)map[n]), (double)g[u]);
+                        if (g[u] != T(0)) atomicAdd(acc + ((code >> 15) & (ADJ_SMEM_REGIONS - 1)), (double)g[u]);
                     } else {
                         An[n].gn = g[u];
                     }
-                    if (!fz) {
-                        const int ns = support_nodes(rec[u], i, j, nx, ny, ms[u]);
+                    // the support nodes from their slots (checked against the grid when the code was made)
+                    const int ns = (int)((code >> 12) & 3u);
 #pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            if (k < ns) fresh[u][k] = release(&An[ms[u][k]], l[u] * w[u][k]);
+                    for (int k = 0; k < 3; ++k) {
+                        const int q = (int)((code >> (4 * k)) & 15u);
+                        ms[u][k] = (unsigned)((int)n + slot_dj(q) * nx + slot_di(q));
+                        if (k < ns) fresh[u][k] = release(&An[ms[u][k]], l[u] * w[u][k]);
                     }
                 }
 #pragma unroll
@@ -517,7 +537,7 @@ static cudaError_t adjoint_t(const AdjLaunch& a, const void* dL_drec, double* gr
         if ((e = cudaMemsetAsync(a.cnt, 0, (size_t)a.nfields * sizeof(unsigned), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(a.head, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
         adj_frontier_flat_kernel<T><<<fgrid, 256, 0, st>>>(a);
-        const int smem_regions = a.nregions <= 512 ? 1 : 0;
+        const int smem_regions = a.nregions <= ADJ_SMEM_REGIONS ? 1 : 0;
         const size_t smem = (smem_regions ? (size_t)8 * a.nregions * sizeof(double) : 0) +
                             (size_t)8 * 2 * ADJ_CAP * sizeof(unsigned);
         adj_warp_kernel<T><<<a.warp_grid, 256, smem, st>>>(a, grad, smem_regions);
