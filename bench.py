@@ -44,15 +44,13 @@ WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 
 # tests/golden/make_ops_per_node.py.  The sweep's roofline divides (this count x the launch's nodes) by the
 # launch's CUDA-event time; the peak is SMs x 128 FP32 lanes x 2 (an FMA is two operations) x SM clock.
 OPS_FILE = os.path.join(ROOT, "tests", "golden", "ops_per_node.txt")
-# DRAM bytes (read + write) per node of the sweep kernel's launch, from one ncu capture of a 2,560-field solve
-# (80 weld samples x 32 sources); scaled to a launch by its nodes.  None for a kernel changed since its capture.
 # DRAM bytes per node of one solve's sweep launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of the solve alone, divided by the launch's nodes; profiles/ holds the captures); None where the
 # kernel has changed since its counters were taken
-TRAFFIC_BYTES_PER_NODE = {"fim_warp_kernel": (2.601624e9 + 3.087003e9) / 147783680,
-                          "fim_cta_kernel<64>": (0.736457472e9 + 1.305613056e9) / 147783680,
+TRAFFIC_BYTES_PER_NODE = {"fim_warp_kernel": (2.619382e9 + 3.100162e9) / 147783680,
+                          "fim_cta_kernel<64>": (0.738537984e9 + 1.305926912e9) / 147783680,
                           "fim_cta_kernel<128>": None, "fim_cta_kernel<256>": None,
-                          "fim_cta_kernel<512>": (8.810240e6 + 0.076032e6) / 2097152}
+                          "fim_cta_kernel<512>": (8.809984e6 + 0.044544e6) / 2097152}
 FP32_LANES = 128
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
 
