@@ -326,6 +326,10 @@ def main():
 
     stage = {}
     side = [torch.cuda.Stream(), torch.cuda.Stream()]
+    # the rays' points packed back to back for the host (alf_pack_rays), into buffers of the worst-case size
+    nrays = P.nfields * P.nrec
+    packed = torch.empty((nrays * P.options.max_ray_points, 2), dtype=torch.float32, device=th.device)
+    offsets = torch.empty(nrays + 1, dtype=torch.int64, device=th.device)
 
     def step(theta):
         # the FP64 check (FP64 pipe) runs inside the solve, each field checked by the CTA that solved it
@@ -346,6 +350,7 @@ def main():
                 mr, fl = P.check64(theta, times, rec)
         with torch.cuda.stream(side[1]):
             rays = P.trace_rays(theta, times)
+            P.pack_rays(rays[0], rays[1], packed=packed, offsets=offsets)
         g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
         for s in side:
             cur.wait_stream(s)
@@ -427,19 +432,26 @@ def main():
 
     # ---- end to end through the public API: orientations from pinned host memory in, receiver times, the
     # gradient and every ray (points, point counts, times, status) back to pinned host memory
+    # (the ray paths leave packed: the offsets, then the total's points; counts are the offsets' differences)
     pts, npts, rtime, rst = res["rays"]
     th_host = torch.from_numpy(np.stack([s.region_theta for s in wl.samples])).pin_memory()
-    outs = [rect, res["grad"], pts, npts, rtime, rst]
+    outs = [rect, res["grad"], offsets, rtime, rst]
     hosts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    packed_host = torch.empty(packed.shape, dtype=packed.dtype).pin_memory()
     th_dev = torch.empty_like(th)
+    d2h = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         th_dev.copy_(th_host, non_blocking=True)
         r = step(th_dev)
-        for h, o in zip(hosts, [rect, r["grad"], *r["rays"]]):
+        for h, o in zip(hosts, [rect, r["grad"], offsets, r["rays"][2], r["rays"][3]]):
             h.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
+        total = int(hosts[2][-1])
+        packed_host[:total].copy_(packed[:total], non_blocking=True)
+        torch.cuda.synchronize()
+        d2h = sum(h.numel() * h.element_size() for h in hosts) + total * 2 * packed.element_size()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     if P.status() != 0:
         raise SystemExit("device status non-zero in the end-to-end steps")
@@ -460,7 +472,7 @@ def main():
         "fp64_check": {"max_rel_residual": float(mr.max().item()), "record_flips": int(fl.sum().item())},
         "e2e": {"value": nodes / (e2e_ms * 1e-3), "unit": "nodes/s",
                 "h2d_bytes_per_step": int(th_host.numel() * th_host.element_size()),
-                "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hosts))},
+                "d2h_bytes_per_step": int(d2h)},
         "roofline": roof,
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
         "gpu_launches": int(launches),

@@ -312,6 +312,21 @@ alf_status alf_trace_rays(alf_plan* plan, const double* region_theta, const void
 alf_status alf_ray_gradient(alf_plan* plan, const double* region_theta, const void* ray_pts, const int32_t* ray_npts,
                             const void* dL_dray, double* dL_dtheta, void* stream);
 
+/* The traced ray paths (Sec. 5.1) packed back to back, for a compact copy or
+ * store: ray r's points are packed_pts[offsets[r] .. offsets[r + 1]).  Only the
+ * points a ray has are read (its count clamped to 0..max_ray_points).
+ *  ray_pts, ray_npts  the output of alf_trace_rays for the same plan, input
+ *  packed_pts         [total points][2], the precision of the plan, output;
+ *                     capacity for nrays * max_ray_points points covers any case
+ *  offsets            [nrays + 1] int64, output: the points of the rays before
+ *                     r (exclusive prefix sum of the counts); offsets[nrays] is
+ *                     the total
+ * nrays = nsamples * nsources * nreceivers, in the order of alf_trace_rays.
+ * Device buffers, caller-owned; asynchronous on `stream`.  Returns
+ * ALF_ERR_INVALID_ARG for a null pointer or a plan without receivers. */
+alf_status alf_pack_rays(alf_plan* plan, const void* ray_pts, const int32_t* ray_npts, void* packed_pts,
+                         int64_t* offsets, void* stream);
+
 /* Adjoint (reverse-mode) gradient of the receiver times: given dL/dT at every
  * receiver, returns dL/dtheta for every region, by differentiating the chosen
  * stencil (or fallback) of every node and the straight-ray initialisation,

@@ -192,6 +192,18 @@ class Plan:
                          C.c_void_p(st.data_ptr()), self._stream())
         return pts, npts, rt, st
 
+    def pack_rays(self, pts, npts, packed=None, offsets=None):
+        """The traced paths back to back: (packed [capacity, 2] in the plan's dtype, offsets [nrays + 1] int64);
+        ray r's points are packed[offsets[r]:offsets[r + 1]], offsets[-1] the total."""
+        nrays = self.nsamples * self.nsrc * self.nrec
+        if packed is None:
+            packed = torch.empty((nrays * self.options.max_ray_points, 2), dtype=self.dtype, device=self._dev())
+        if offsets is None:
+            offsets = torch.empty(nrays + 1, dtype=torch.int64, device=self._dev())
+        B.alf_pack_rays(self.ctx, self.plan, C.c_void_p(pts.data_ptr()), C.c_void_p(npts.data_ptr()),
+                        C.c_void_p(packed.data_ptr()), C.c_void_p(offsets.data_ptr()), self._stream())
+        return packed, offsets
+
     def ray_gradient(self, theta, pts, npts, dL_dray):
         """dL/dtheta [nsamples, nregions] (float64) from dL/dT of every ray, its path (from trace_rays) held
         fixed."""

@@ -27,7 +27,8 @@ EXPORTS = ("alf_default_options", "alf_create", "alf_destroy", "alf_last_error",
            "alf_plan_destroy", "alf_plan_field_offset", "alf_plan_nfields", "alf_plan_options", "alf_solve",
            "alf_check64", "alf_trace_rays", "alf_backward", "alf_sync_status", "alf_plan_stats", "alf_plan_autotune",
            "alf_eval_velocity", "alf_solve_field_noalloc", "alf_ray_gradient", "alf_check64_nodes",
-           "alf_solve_check64")
+           "alf_solve_check64",
+           "alf_pack_rays")
 
 
 class AlfError(RuntimeError):
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
         L.alf_solve_check64.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.alf_trace_rays.restype = C.c_int
         L.alf_trace_rays.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.alf_pack_rays.restype = C.c_int
+        L.alf_pack_rays.argtypes = [vp, vp, vp, vp, vp, vp]
         L.alf_ray_gradient.restype = C.c_int
         L.alf_ray_gradient.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.alf_backward.restype = C.c_int
@@ -199,6 +202,10 @@ def alf_check64_nodes(ctx, plan, theta_ptr, times_ptr, records_ptr, ctimes_ptr, 
                       stream):
     _check(ctx, load().alf_check64_nodes(plan, theta_ptr, times_ptr, records_ptr, ctimes_ptr, crec_ptr, max_rel_ptr,
                                          flips_ptr, stream))
+
+
+def alf_pack_rays(ctx, plan, pts_ptr, npts_ptr, packed_ptr, offsets_ptr, stream):
+    _check(ctx, load().alf_pack_rays(plan, pts_ptr, npts_ptr, packed_ptr, offsets_ptr, stream))
 
 
 def alf_trace_rays(ctx, plan, theta_ptr, times_ptr, pts_ptr, npts_ptr, time_ptr, status_ptr, stream):

@@ -308,6 +308,7 @@ static void plan_free(alf_plan* p)
     dfree(p->d_regions64);
     dfree(p->d_q);
     dfree(p->d_ray_error);
+    dfree(p->d_ray_blocks);
     dfree(p->d_frozen);
     if (p->h_q) cudaFreeHost(p->h_q);
 }
@@ -642,6 +643,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     ALLOC(p->d_rec, (size_t)p->B * p->Rr * 2);
     ALLOC(p->d_q, 1);
     ALLOC(p->d_ray_error, 4);
+    ALLOC(p->d_ray_blocks, ((size_t)p->nfields * p->Rr + 1023) / 1024 + 1);
     ALLOC(p->d_frozen, (size_t)p->nfields * fw);
     {
         char* r1 = nullptr;
@@ -975,6 +977,21 @@ alf_status alf_trace_rays(alf_plan* p, const double* theta, const void* times, v
     a.error = p->d_ray_error;
     a.h_of_sample = p->d_h;
     ALF_CUDA(ctx, launch_rays(p->opt.precision, a, st));
+    return ALF_OK;
+}
+
+alf_status alf_pack_rays(alf_plan* p, const void* ray_pts, const int32_t* ray_npts, void* packed_pts,
+                         int64_t* offsets, void* stream)
+{
+    if (!p) return ALF_ERR_INVALID_ARG;
+    alf_ctx* ctx = p->ctx;
+    if (!ray_pts || !ray_npts || !packed_pts || !offsets)
+        return fail(ctx, ALF_ERR_INVALID_ARG, "alf_pack_rays: null ray_pts, ray_npts, packed_pts or offsets");
+    if (p->Rr == 0) return fail(ctx, ALF_ERR_INVALID_ARG, "alf_pack_rays: plan has no receivers");
+    ALF_CUDA(ctx, cudaSetDevice(ctx->device));
+    ALF_CUDA(ctx, launch_pack_rays(p->opt.precision, ray_pts, ray_npts, (long long)p->nfields * p->Rr,
+                                   p->opt.max_ray_points, p->d_ray_blocks, packed_pts, (long long*)offsets,
+                                   ctx->nsm * 16, as_stream(stream)));
     return ALF_OK;
 }
 

@@ -202,6 +202,9 @@ struct RayLaunch {
     unsigned* error;
 };
 cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st);
+// packed ray points: offsets[nrays + 1] (int64) and the points back to back; block_sums: (nrays + 1023) / 1024 + 1
+cudaError_t launch_pack_rays(int precision, const void* pts, const int32_t* npts, long long nrays, int max_pts,
+                             long long* block_sums, void* packed, long long* offsets, int grid, cudaStream_t st);
 // gradient of the ray times along the given paths (a.pts, a.npts) by the region orientations
 cudaError_t launch_ray_gradient(int precision, const RayLaunch& a, const void* dL_dray, double* grad, int nsamples,
                                 cudaStream_t st);
@@ -292,6 +295,7 @@ struct alf_plan {
     void* d_adj_nodes = nullptr;    // AdjNode<T> per node (32 B FP32, 64 B FP64)
     alf::QueueState* d_q = nullptr;
     unsigned* d_ray_error = nullptr;
+    long long* d_ray_blocks = nullptr;  // block sums of alf_pack_rays' scan ((nrays + 1023) / 1024 + 1)
     unsigned* d_frozen = nullptr;  // per-field bitmap of frozen nodes in the source box
     alf::QueueState* h_q = nullptr;  // pinned
 };

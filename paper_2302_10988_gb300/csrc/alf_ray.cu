@@ -17,6 +17,8 @@
 // and stops within stop_radius cells of the target, which is appended.
 // The time along the finished polyline is integrated through the
 // nearest-node cells (each segment split at x = k + 1/2, y = k + 1/2).
+#include <type_traits>
+
 #include "alf_internal.h"
 
 namespace alf {
@@ -420,6 +422,114 @@ cudaError_t launch_rays(int precision, const RayLaunch& a, cudaStream_t st)
     if (precision == ALF_FP64) ray_kernel<double><<<(unsigned)gs, bs, 0, st>>>(a);
     else ray_kernel<float><<<(unsigned)gs, bs, 0, st>>>(a);
     note_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Packing of the traced rays (alf_pack_rays): offsets[r] = the points of the rays before r (an exclusive
+// prefix sum of the point counts, in blocks of ALF_PACK_BLOCK rays: every block's sum, one block's scan of
+// those sums, every block's own scan), then one warp per ray copies its points behind those of the rays
+// before it.  A ray's slots past its count are not read, so the copy moves only the path's points.
+// ---------------------------------------------------------------------------
+#define ALF_PACK_BLOCK 1024
+
+ALF_D long long ray_count(const int32_t* npts, long long r, int max_pts)
+{
+    const int n = npts[r];
+    return n < 0 ? 0 : (n > max_pts ? max_pts : n);
+}
+
+// inclusive scan of v over the block (blockDim.x = ALF_PACK_BLOCK); returns this thread's inclusive sum
+ALF_D long long block_inclusive_scan(long long v, long long* s_warp)
+{
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v += y;
+    }
+    if (lane == 31u) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < (blockDim.x >> 5) ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if ((int)lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) v += s_warp[wid - 1];
+    return v;
+}
+
+__global__ void __launch_bounds__(ALF_PACK_BLOCK) ray_block_sums_kernel(const int32_t* npts, long long nrays,
+                                                                         int max_pts, long long* block_sums)
+{
+    __shared__ long long s_warp[32];
+    const long long r = (long long)blockIdx.x * ALF_PACK_BLOCK + threadIdx.x;
+    const long long v = block_inclusive_scan(r < nrays ? ray_count(npts, r, max_pts) : 0, s_warp);
+    if (threadIdx.x == ALF_PACK_BLOCK - 1) block_sums[blockIdx.x] = v;
+}
+
+// exclusive scan of the block sums in place, by one block; block_sums[nblocks] = the total
+__global__ void __launch_bounds__(ALF_PACK_BLOCK) ray_scan_sums_kernel(long long* block_sums, long long nblocks)
+{
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nblocks; base += ALF_PACK_BLOCK) {
+        const long long k = base + threadIdx.x;
+        const long long v = k < nblocks ? block_sums[k] : 0;
+        const long long incl = block_inclusive_scan(v, s_warp);
+        const long long carry = s_carry;
+        if (k < nblocks) block_sums[k] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == ALF_PACK_BLOCK - 1) s_carry = carry + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_sums[nblocks] = s_carry;
+}
+
+__global__ void __launch_bounds__(ALF_PACK_BLOCK) ray_offsets_kernel(const int32_t* npts, long long nrays, int max_pts,
+                                                                      const long long* block_off, long long* offsets)
+{
+    __shared__ long long s_warp[32];
+    const long long r = (long long)blockIdx.x * ALF_PACK_BLOCK + threadIdx.x;
+    const long long v = r < nrays ? ray_count(npts, r, max_pts) : 0;
+    const long long incl = block_inclusive_scan(v, s_warp);
+    if (r < nrays) offsets[r] = block_off[blockIdx.x] + incl - v;
+    if (r == nrays - 1) offsets[nrays] = block_off[blockIdx.x] + incl;
+}
+
+template <typename T>
+__global__ void ray_pack_kernel(const T* pts, const int32_t* npts, long long nrays, int max_pts,
+                                const long long* offsets, T* packed)
+{
+    using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const long long warps = (long long)gridDim.x * blockDim.x / 32;
+    const unsigned lane = threadIdx.x & 31u;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < nrays; r += warps) {
+        const long long n = ray_count(npts, r, max_pts), off = offsets[r];
+        const T2* src = (const T2*)pts + r * max_pts;
+        T2* dst = (T2*)packed + off;
+        for (long long k = lane; k < n; k += 32) dst[k] = src[k];
+    }
+}
+
+cudaError_t launch_pack_rays(int precision, const void* pts, const int32_t* npts, long long nrays, int max_pts,
+                             long long* block_sums, void* packed, long long* offsets, int grid, cudaStream_t st)
+{
+    if (nrays <= 0) return cudaMemsetAsync(offsets, 0, sizeof(long long), st);
+    const long long nb = (nrays + ALF_PACK_BLOCK - 1) / ALF_PACK_BLOCK;
+    ray_block_sums_kernel<<<(unsigned)nb, ALF_PACK_BLOCK, 0, st>>>(npts, nrays, max_pts, block_sums);
+    ray_scan_sums_kernel<<<1, ALF_PACK_BLOCK, 0, st>>>(block_sums, nb);
+    ray_offsets_kernel<<<(unsigned)nb, ALF_PACK_BLOCK, 0, st>>>(npts, nrays, max_pts, block_sums, offsets);
+    if (precision == ALF_FP64)
+        ray_pack_kernel<double><<<grid, 256, 0, st>>>((const double*)pts, npts, nrays, max_pts, offsets, (double*)packed);
+    else
+        ray_pack_kernel<float><<<grid, 256, 0, st>>>((const float*)pts, npts, nrays, max_pts, offsets, (float*)packed);
+    note_launches(4);
     return cudaGetLastError();
 }
 

@@ -158,3 +158,25 @@ def test_ray_gradient_agrees_with_adjoint(api):
         rel = float(np.linalg.norm(a - r) / np.linalg.norm(a))
         print(f"sample {b}: cosine {cos:.4f}, relative difference {rel:.3f}")
         assert cos > 0.95 and rel < 0.3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_pack_rays(api, precision):
+    """alf_pack_rays: offsets are the exclusive prefix sum of the point counts and every ray's points come
+    back unchanged behind those of the rays before it; an uneven batch with rays of many lengths, several
+    scan blocks of 1024 rays."""
+    wl = W.weld_batch(nsamples=6, nsrc=16, nrec=24, sizes=(64, 96, 128))
+    P = api.Plan(wl, precision=precision)
+    th = P.theta_tensor()
+    times, _ = P.solve(th)
+    pts, npts, rtime, st = P.trace_rays(th, times)
+    packed, offs = P.pack_rays(pts, npts)
+    assert P.status() == 0
+    n = npts.cpu().numpy().reshape(-1).astype(np.int64)
+    o = offs.cpu().numpy()
+    assert n.size == 6 * 16 * 24 and o.size == n.size + 1
+    assert o[0] == 0 and np.array_equal(np.diff(o), n)
+    p = pts.cpu().numpy().reshape(n.size, -1, 2)
+    q = packed.cpu().numpy()
+    for r in range(n.size):
+        assert np.array_equal(q[o[r]:o[r + 1]], p[r, :n[r]])
