@@ -239,7 +239,7 @@ ALF_D bool warp_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& e
 // The dirty bitmap is in shared memory (rank 0's) or in global memory.
 // ---------------------------------------------------------------------------
 struct CtaSweepShared {
-    unsigned cnt[2];       // evaluation / carried (then marked) list sizes of the round
+    unsigned cnt[3];       // near evaluation / carried (then marked) / far evaluation list sizes of the round
     unsigned long long kmin[32];
 };
 
@@ -368,6 +368,7 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
         if (tid == 0) {
             S.cnt[0] = 0u;
             S.cnt[1] = 0u;
+            S.cnt[2] = 0u;
         }
         sweep_sync<CS>();
         auto mm = order_key(inf);
@@ -380,31 +381,40 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
         } else {
             mm = (decltype(mm))S.kmin[par];
         }
-        const T lim = from_key(mm, T(0)) + g.band;
-        // split
+        const T front = from_key(mm, T(0));
+        const T lim = front + g.band, near = front + T(0.5) * g.band;
+        // split: the entries in the band (or without a value) are evaluated, those in its nearer half at the
+        // front of the evaluation list and the rest from its back, so that the first passes of the round take
+        // the earliest nodes and later ones see their new values; the rest stay
+        const unsigned last = (unsigned)(nx * ny) - 1u;
         for (unsigned base = 0; base < nact; base += STRIDE) {
             const unsigned k = base + tid;
             const bool in = k < nact;
-            bool ev = false;
+            bool ev = false, nr = false;
             unsigned n = 0u;
             if (in) {
                 n = LA[k];
                 const T t = tf[n];
                 ev = t <= lim || !(t < inf);
+                nr = t <= near;
             }
-            const unsigned se = reserve<T>(&S.cnt[0], in && ev, below);
+            const unsigned sn = reserve<T>(&S.cnt[0], in && ev && nr, below);
+            const unsigned sf = reserve<T>(&S.cnt[2], in && ev && !nr, below);
             const unsigned sc = reserve<T>(&S.cnt[1], in && !ev, below);
             if (in && ev) {
-                g.el[se] = n;
+                g.el[nr ? sn : last - sf] = n;
                 atomicAnd(g.bm + (n >> 5), ~(1u << (n & 31u)));
             } else if (in) {
                 LB[sc] = n;
             }
         }
         sweep_sync<CS>();
-        const unsigned ne = S.cnt[0];
+        // entry e of the round: el[e] below nnear, el[last - (e - nnear)] after (the two parts never meet: the
+        // dirty set holds each node once); its values before and after at the same index
+        const unsigned nnear = S.cnt[0], ne = S.cnt[0] + S.cnt[2];
         // evaluate
-        for (unsigned e = tid; e < ne; e += STRIDE) {
+        for (unsigned e0 = tid; e0 < ne; e0 += STRIDE) {
+            const unsigned e = e0 < nnear ? e0 : last - (e0 - nnear);
             const unsigned n = g.el[e];
             const int i = (int)(n % (unsigned)nx), j = (int)(n / (unsigned)nx);
             const SlotInGrid in = slots_in_grid(i, j, nx, ny);
@@ -430,11 +440,12 @@ ALF_D bool cta_sweep(const WarpGrid<T>& g, unsigned nact, unsigned long long& ev
         // marking: a thread's push decisions first (plain loads), then its dirty-bit test-and-sets (issued
         // independently of one another), then one slot reservation per warp (prefix sum of the counts)
         for (unsigned base = 0; base < ne; base += STRIDE) {
-            const unsigned e = base + tid;
+            const unsigned e0 = base + tid;
+            const unsigned e = e0 < nnear ? e0 : last - (e0 - nnear);
             unsigned pm = 0u;  // bit q < 12: neighbour q; bit 12: the node itself (seeds later)
             int i = 0, j = 0;
             unsigned n = 0u;
-            if (e < ne) {
+            if (e0 < ne) {
                 const T o = g.ov[e];
                 const T v = g.nv[e];
                 const bool changed = !same_bits(o, v);
