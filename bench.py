@@ -48,9 +48,8 @@ OPS_FILE = os.path.join(ROOT, "tests", "golden", "ops_per_node.txt")
 # capture of the solve alone, divided by the launch's nodes; profiles/ holds the captures); None where the
 # kernel has changed since its counters were taken
 TRAFFIC_BYTES_PER_NODE = {"fim_warp_kernel": (2.619382e9 + 3.100162e9) / 147783680,
-                          "fim_cta_kernel<64>": (0.738537984e9 + 1.305926912e9) / 147783680,
-                          "fim_cta_kernel<128>": None, "fim_cta_kernel<256>": None,
-                          "fim_cta_kernel<512>": (8.809984e6 + 0.044544e6) / 2097152}
+                          "fim_cta_kernel<64>": (0.749040896e9 + 1.390257152e9) / 147783680,
+                          "fim_cta_kernel<128>": None, "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
 FP32_LANES = 128
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
 
