@@ -366,8 +366,11 @@ __global__ void adj_process_kernel(AdjLaunch a, int parity)
 #define ADJ_U 4      // frontier entries per lane per pass of the field-resident adjoint
 #define ADJ_CAP 256  // frontier entries a warp keeps in shared memory per list
 
+// FP32 fields: registers are capped at 48 (a bound of five CTAs of 256 threads; the kernel runs two per
+// SM), so that two CTAs fit beside the two of the FP64 check, which runs on another stream after the solve.
 template <typename T>
-__global__ void __launch_bounds__(256) adj_warp_kernel(AdjLaunch a, double* grad, int smem_regions)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1)
+    adj_warp_kernel(AdjLaunch a, double* grad, int smem_regions)
 {
     extern __shared__ double s_acc[];
     constexpr unsigned FULL = 0xffffffffu;

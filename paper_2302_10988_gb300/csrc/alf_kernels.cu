@@ -951,11 +951,15 @@ cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields,
 // check64: F in double precision at every node of a solved field (alf_check.cuh).  Frozen
 // nodes come from the per-field bitmap of the initialisation box.
 // ---------------------------------------------------------------------------
+// FP32 fields: registers are capped at 80 (a bound of three CTAs of 256 threads) while the kernel runs two
+// CTAs per SM.  The two take 40,960 of the SM's 65,536 registers and leave room for two CTAs of the adjoint
+// sweep (24,576), so that the check and the adjoint, on separate streams after the solve, share the SMs (a
+// step of the weld batch 495.6 -> 491.6 ms; the check alone 110 -> 115 ms, with a little spilling).
 template <typename T, bool VT>
-__global__ void check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint32_t* region_map,
-                               const RegionP<double>* regions, int nregions, const uint8_t* records,
-                               const unsigned* frozen_bits, int box, double* max_rel, int32_t* n_flips,
-                               double* F_out, uint8_t* rec_out)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+    check64_kernel(const T* times, const FieldDesc* fields, int nfields, const uint32_t* region_map,
+                   const RegionP<double>* regions, int nregions, const uint8_t* records, const unsigned* frozen_bits,
+                   int box, double* max_rel, int32_t* n_flips, double* F_out, uint8_t* rec_out)
 {
     // persistent: the CTAs stride over (field, chunk) work items, so that a small grid leaves room on
     // the SMs for kernels of other streams while this one keeps the FP64 pipe busy
