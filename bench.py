@@ -78,8 +78,8 @@ def _args():
                          "one step, a short summary line (for ncu)")
     ap.add_argument("--profile-stages", default="all", choices=["all", "solve"],
                     help="profiling run: the whole step, or the travel-time solve alone")
-    ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="profiling run: sweep schedule (0: the library's choice)")
+    ap.add_argument("--sweep", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="profiling run: sweep schedule (0: the library's choice; 4: active tiles)")
     ap.add_argument("--band", type=float, default=1.5,
                     help="profiling run: front band of the sweep in cell-crossing times")
     ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 64, 128, 256, 512],
@@ -242,7 +242,7 @@ def profile_run(args, wl, api, local):
 
 
 def _kernel_name(opts) -> str:
-    kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel"}[opts.sweep]
+    kname = {1: "fim_eval_kernel", 2: "fim_warp_kernel", 3: "fim_cta_kernel", 4: "fim_tile_kernel"}[opts.sweep]
     if opts.sweep == 3:  # the CTA shape decides how many fields share the L2, hence the traffic
         kname += f"<{opts.cta_threads}>" + (f"x{opts.cta_cluster}" if opts.cta_cluster > 1 else "")
     return kname

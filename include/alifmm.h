@@ -114,8 +114,11 @@ typedef struct {
                                kernels over the whole batch; 2 = one warp owns each field and runs all
                                its rounds inside one launch (suits many fields; needs nx*ny/8 bytes of
                                shared memory per warp, nx*ny <= 2^18); 3 = one CTA owns each field,
-                               one launch (suits few large fields); 0 = choose (2 when it fits and the
-                               fields fill the GPU, else 3), default 0 */
+                               one launch (suits few large fields); 4 = active tiles: one CTA per field
+                               iterates F on 8 x 8 tiles in shared memory until no node of a tile changes
+                               and wakes the neighbouring tiles that read a changed border (no front band;
+                               never chosen by 0 or by alf_plan_autotune); 0 = choose (2 when it fits and
+                               the fields fill the GPU, else 3), default 0 */
     int ray_family;         /* planes of the ray tracer (Sec. 5.1): 0 = the set most perpendicular to the
                                ray at every step (default); 1..4 = one fixed set: x = c, y = c, x - y = c,
                                x + y = c; 5 = the fastest of the four fixed sets (Table 3 compares them) */

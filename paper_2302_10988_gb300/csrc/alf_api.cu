@@ -341,7 +341,7 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     } else {
         return fail(ctx, ALF_ERR_INVALID_ARG, "unknown init_mode %d", opt.init_mode);
     }
-    if (opt.sweep < 0 || opt.sweep > 3) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1, 2 or 3");
+    if (opt.sweep < 0 || opt.sweep > 4) return fail(ctx, ALF_ERR_INVALID_ARG, "sweep must be 0, 1, 2, 3 or 4");
     if (opt.ray_family < 0 || opt.ray_family > 5) return fail(ctx, ALF_ERR_INVALID_ARG, "ray_family must be in 0..5");
     if (opt.velocity_table != 0 && opt.velocity_table != 1)
         return fail(ctx, ALF_ERR_INVALID_ARG, "velocity_table must be 0 or 1");
@@ -546,6 +546,17 @@ alf_status alf_plan_create(alf_ctx* ctx, const alf_geometry* g, const alf_option
     // CTA-per-field sweep: shared bitmap when the largest field's fits in 64 KB, else global bitmaps
     p->cta_words = (unsigned)std::min<size_t>((p->max_field_nodes + 31) / 32, 16384);
     if (p->cta_words < (p->max_field_nodes + 31) / 32) p->cta_words = 0;
+    // active-tile sweep: tile bitmaps in shared memory up to 16 KB, else the fields' global bitmaps
+    {
+        unsigned tw = 0;
+        for (const auto& fd : p->fields) tw = std::max(tw, fim_tile_words(fd.nx, fd.ny));
+        p->tile_words = tw <= 4096u ? tw : 0u;
+        p->tile_grid = fim_tile_grid(opt.precision, p->tile_words, opt.velocity_table != 0, ctx->nsm);
+    }
+    if (opt.sweep == 4 && p->tile_grid == 0) {
+        delete p;
+        return fail(ctx, ALF_ERR_UNSUPPORTED, "sweep = 4: the active-tile kernel cannot be launched");
+    }
     // default: a whole SM per field when the fields do not outnumber the SMs (FP32), and a cluster of 2, 4 or
     // 8 SMs per field when they leave that many SMs per field idle and the fields are large (>= 2^19 nodes
     // per SM of the cluster: on smaller fields a round is one evaluation's latency plus the cluster barrier,
@@ -845,7 +856,7 @@ static alf_status solve_impl(alf_plan* p, const double* theta, void* times, void
         a.max_rel = max_rel;
         a.n_flips = n_flips;
     }
-    if (p->sweep_mode == 2 || p->sweep_mode == 3) {
+    if (p->sweep_mode >= 2) {
         // field-resident sweep: the whole fixed-point iteration in one launch
         const bool timing = p->opt.time_kernels != 0;
         if (timing && p->ev.size() < 2) {
@@ -854,6 +865,8 @@ static alf_status solve_impl(alf_plan* p, const double* theta, void* times, void
         }
         if (timing) ALF_CUDA(ctx, cudaEventRecord(p->ev[0], st));
         if (p->sweep_mode == 2) ALF_CUDA(ctx, launch_fim_warp(prec, a, p->d_order, p->warp_words, p->warp_grid, st));
+        else if (p->sweep_mode == 4)
+            ALF_CUDA(ctx, launch_fim_tile(prec, a, p->d_order, p->tile_words, p->tile_grid, st));
         else
             ALF_CUDA(ctx, launch_fim_cta(prec, a, p->d_order, p->cta_words, p->cta_grid, p->cta_threads, p->cta_cluster,
                                          st, fused));

@@ -102,6 +102,12 @@ cudaError_t launch_fim_cta(int precision, const FimLaunch& a, const unsigned* or
 // the CTA sweep can run each field's FP64 check itself (FP32, no velocity table, one CTA per field)
 bool fim_cta_can_check(int precision, int vtable, int cluster);
 int fim_cta_grid(int precision, unsigned smem_words, bool vt, int threads, int cluster, int nsm);  // CTAs; 0: none
+// active-tile sweep (alf_tile.cu): one CTA of 8 warps per field, 8 x 8 tiles iterated in shared memory; the
+// tile bitmap of a field in shared memory when it has at most smem_words words (fim_tile_words), else global
+cudaError_t launch_fim_tile(int precision, const FimLaunch& a, const unsigned* order, unsigned smem_words, int grid,
+                            cudaStream_t st);
+int fim_tile_grid(int precision, unsigned smem_words, bool vt, int nsm);  // CTAs resident at once; 0: none
+unsigned fim_tile_words(int nx, int ny);                                  // words of a field's tile bitmap
 cudaError_t launch_finalize(int precision, void* times, const FieldDesc* fields, int nfields, int box,
                             const int32_t* rec_ij, int nsrc, int nrec, void* rec_times, uint8_t* records,
                             cudaStream_t st);
@@ -265,9 +271,12 @@ struct alf_plan {
     unsigned long long* h_pending = nullptr;  // pinned
     int rounds_per_check = 32;
     // field-resident sweep (option sweep = 2, or chosen by sweep = 0)
-    int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field, 3: one CTA per field
+    int sweep_mode = 1;             // 1: bulk-synchronous rounds, 2: one warp per field, 3: one CTA per field,
+                                    // 4: active tiles, one CTA per field
     unsigned cta_words = 0;         // shared bitmap words of the CTA-per-field sweep
     int cta_grid = 0;
+    unsigned tile_words = 0;        // shared tile-bitmap words of the active-tile sweep (0: global bitmaps)
+    int tile_grid = 0;              // its CTAs resident at once (0: it cannot run)
     int cta_threads = 256;          // threads of one field's CTA: 64, 128, 256 or 512
     int cta_default = 256;          // the plan's choice when the options leave it open
     int cta_cluster = 1;            // CTAs (of 512 threads) sharing one field: 1, 2, 4 or 8

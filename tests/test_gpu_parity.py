@@ -62,7 +62,7 @@ def test_homogeneous_ti_fp64(api, oracle, group):
     assert np.allclose(rt.cpu().numpy()[0, 0], tau[r[:, 1], r[:, 0]], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("sweep", [1, 2, 3])
+@pytest.mark.parametrize("sweep", [1, 2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
 def test_weld_ragged_parity(api, oracle, precision, tol, sweep):
     wl = W.weld_single(n=100, h=0.5e-3, rg=5, seed=12, nsrc=3, nrec=5)
@@ -81,7 +81,7 @@ def test_weld_ragged_parity(api, oracle, precision, tol, sweep):
         print(f"{precision} band={band}: record flips {flips}")
 
 
-@pytest.mark.parametrize("sweep", [1, 2, 3])
+@pytest.mark.parametrize("sweep", [1, 2, 3, 4])
 def test_tiny_and_edge_grids(api, oracle, sweep):
     for (nx, ny, si, sj) in [(2, 2, 0, 0), (3, 7, 2, 6), (33, 9, 32, 0), (65, 17, 0, 16), (40, 40, 20, 20)]:
         rm = np.zeros((ny, nx), np.uint16)
@@ -190,14 +190,16 @@ def test_graph_stream_and_timing(api, oracle):
 
 
 def test_sweep_schedules_agree(api, oracle):
-    """Both sweep schedules reach the unique fixed point of F: in FP64 their fields and records are identical
-    bit for bit, on a batch of uneven fields, and they match the oracle."""
+    """Every sweep schedule (lockstep rounds, warp per field, CTA per field, active tiles) reaches the unique
+    fixed point of F: in FP64 their fields and records are identical bit for bit, on a batch of uneven
+    fields, and they match the oracle."""
     wl = W.weld_batch(nsamples=6, nsrc=4, nrec=4, sizes=(32, 64, 96, 128))
     P1, th, t1, _, rec1 = _solve(api, wl, "fp64", sweep=1)
     P2, _, t2, _, rec2 = _solve(api, wl, "fp64", sweep=2)
     P3, _, t3, _, rec3 = _solve(api, wl, "fp64", sweep=3)
-    assert torch.equal(t1, t2) and torch.equal(t1, t3)
-    assert torch.equal(rec1, rec2) and torch.equal(rec1, rec3)
+    P4, _, t4, _, rec4 = _solve(api, wl, "fp64", sweep=4)
+    assert torch.equal(t1, t2) and torch.equal(t1, t3) and torch.equal(t1, t4)
+    assert torch.equal(rec1, rec2) and torch.equal(rec1, rec3) and torch.equal(rec1, rec4)
     for nt in (64, 128, 512):  # other numbers of warps on each field's CTA
         Pn, _, tn, _, recn = _solve(api, wl, "fp64", sweep=3, cta_threads=nt, cta_cluster=1)
         assert Pn.options.cta_threads == nt
@@ -210,6 +212,18 @@ def test_sweep_schedules_agree(api, oracle):
         tau, orec, fr, M = oracle_field(oracle, wl, b, s)
         assert rel_err(P2.field(t2, b * 4 + s).cpu().numpy(), tau).max() < 1e-6
         assert record_mismatch(P2.field(rec2, b * 4 + s).cpu().numpy(), orec, fr) == 0
+
+
+def test_tile_sweep_fp32_matches_cta_sweep(api):
+    """The active-tile schedule (8 x 8 tiles iterated in shared memory, no front band) reaches the fixed point
+    the CTA sweep reaches, in FP32 too: fields and records identical bit for bit on uneven fields with the
+    sources on the edges and inside, and the same travel times at the receivers."""
+    wl = W.weld_batch(nsamples=4, nsrc=3, nrec=4, sizes=(40, 96, 130))
+    wl.samples[1].src[1] = [wl.samples[1].nx // 2, wl.samples[1].ny // 2]
+    P3, th, t3, rt3, rec3 = _solve(api, wl, "fp32", sweep=3)
+    P4, _, t4, rt4, rec4 = _solve(api, wl, "fp32", sweep=4)
+    assert P4.options.sweep == 4
+    assert torch.equal(t3, t4) and torch.equal(rec3, rec4) and torch.equal(rt3, rt4)
 
 
 @pytest.mark.parametrize("cs", [2, 4])

@@ -93,11 +93,11 @@ def test_velocity_table_backward_is_refused(api):
 
 def test_velocity_table_schedules_agree(api):
     """The velocity-table kernels of every schedule (lockstep rounds, warp per field, CTA per field of each
-    size, clusters) reach the same fixed point: FP64 fields and records identical bit for bit."""
+    size, clusters, active tiles) reach the same fixed point: FP64 fields and records identical bit for bit."""
     wl = W.weld_batch(nsamples=3, nsrc=2, nrec=3, sizes=(48, 96))
     ref = None
     for opts in ({"sweep": 1}, {"sweep": 2}, {"sweep": 3, "cta_threads": 64, "cta_cluster": 1},
-                 {"sweep": 3, "cta_threads": 256, "cta_cluster": 1}, {"sweep": 3, "cta_cluster": 2}):
+                 {"sweep": 3, "cta_threads": 256, "cta_cluster": 1}, {"sweep": 3, "cta_cluster": 2}, {"sweep": 4}):
         P = api.Plan(wl, precision="fp64", velocity_table=1, **opts)
         th = P.theta_tensor()
         rec = P.new_records()
