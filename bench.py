@@ -330,11 +330,12 @@ def main():
     packed = torch.empty((nrays * P.options.max_ray_points, 2), dtype=torch.float32, device=th.device)
     offsets = torch.empty(nrays + 1, dtype=torch.int64, device=th.device)
 
-    def step(theta):
+    def step(theta, host=None):
         # the FP64 check (FP64 pipe) runs inside the solve, each field checked by the CTA that solved it
         # (--check fused), or after the solve on a stream of its own; the rays (FP32) and the adjoint (memory)
         # are independent of each other and of the check: they run on two more streams, and the step ends
-        # when all have
+        # when all have.  With `host` (the end-to-end leg), the rays' offsets, times and status leave for
+        # pinned host memory on the rays' stream as soon as they are packed, beside the check and the adjoint
         cur = torch.cuda.current_stream()
         if args.check == "fused":
             _, _, mr, fl = P.solve_check64(theta, times=times, rec_times=rect, records=rec)
@@ -350,6 +351,10 @@ def main():
         with torch.cuda.stream(side[1]):
             rays = P.trace_rays(theta, times)
             P.pack_rays(rays[0], rays[1], packed=packed, offsets=offsets)
+            if host is not None:
+                for h, o in zip(host["rays"], [offsets, rays[2], rays[3]]):
+                    h.copy_(o, non_blocking=True)
+                host["rays_out"].record(side[1])
         g = P.backward(theta, times, rec, 2.0 * (rect - t_obs))
         for s in side:
             cur.wait_stream(s)
@@ -431,11 +436,14 @@ def main():
 
     # ---- end to end through the public API: orientations from pinned host memory in, receiver times, the
     # gradient and every ray (points, point counts, times, status) back to pinned host memory
-    # (the ray paths leave packed: the offsets, then the total's points; counts are the offsets' differences)
+    # (the ray paths leave packed: the offsets, then the total's points; counts are the offsets' differences).
+    # The rays' outputs leave while the check and the adjoint still run: the host waits for the offsets
+    # alone, then queues the packed points on the rays' stream.
     pts, npts, rtime, rst = res["rays"]
     th_host = torch.from_numpy(np.stack([s.region_theta for s in wl.samples])).pin_memory()
-    outs = [rect, res["grad"], offsets, rtime, rst]
-    hosts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    pinned = lambda o: torch.empty(o.shape, dtype=o.dtype).pin_memory()
+    host = {"rays": [pinned(offsets), pinned(rtime), pinned(rst)], "rays_out": torch.cuda.Event()}
+    rect_host, grad_host = pinned(rect), pinned(res["grad"])
     packed_host = torch.empty(packed.shape, dtype=packed.dtype).pin_memory()
     th_dev = torch.empty_like(th)
     d2h = 0
@@ -443,14 +451,16 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         th_dev.copy_(th_host, non_blocking=True)
-        r = step(th_dev)
-        for h, o in zip(hosts, [rect, r["grad"], offsets, r["rays"][2], r["rays"][3]]):
-            h.copy_(o, non_blocking=True)
+        r = step(th_dev, host)
+        host["rays_out"].synchronize()
+        total = int(host["rays"][0][-1])
+        with torch.cuda.stream(side[1]):
+            packed_host[:total].copy_(packed[:total], non_blocking=True)
+        rect_host.copy_(rect, non_blocking=True)
+        grad_host.copy_(r["grad"], non_blocking=True)
         torch.cuda.synchronize()
-        total = int(hosts[2][-1])
-        packed_host[:total].copy_(packed[:total], non_blocking=True)
-        torch.cuda.synchronize()
-        d2h = sum(h.numel() * h.element_size() for h in hosts) + total * 2 * packed.element_size()
+        d2h = (sum(h.numel() * h.element_size() for h in host["rays"] + [rect_host, grad_host]) +
+               total * 2 * packed.element_size())
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     if P.status() != 0:
         raise SystemExit("device status non-zero in the end-to-end steps")
@@ -462,7 +472,7 @@ def main():
         "config": {"workload": WORKLOAD, "fields": P.nfields, "nodes_per_step": P.total_nodes,
                    "rays_per_step": P.nfields * P.nrec, "band_cells": P.options.band_cells,
                    "sweep": {1: "lockstep rounds over all fields", 2: "one warp per field",
-                             3: "one CTA per field"}[P.options.sweep],
+                             3: "one CTA per field", 4: "active tiles"}[P.options.sweep],
                    "cuda_graph": graph is not None,
                    "fp64_check": {"fused": "inside the sweep kernel, per field after its sweep",
                                   "stream": "own kernel on a side stream after the solve"}[args.check],
