@@ -45,11 +45,13 @@ WORKLOAD = ("weld batch: 512 samples x 32 sources, n in 128..320 step 32, 10x10 
 # launch's CUDA-event time; the peak is SMs x 128 FP32 lanes x 2 (an FMA is two operations) x SM clock.
 OPS_FILE = os.path.join(ROOT, "tests", "golden", "ops_per_node.txt")
 # DRAM bytes per node of one solve's sweep launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of the solve alone, divided by the launch's nodes; profiles/ holds the captures); None where the
-# kernel has changed since its counters were taken
+# capture of an FP32 solve alone, divided by the launch's nodes; profiles/ holds the captures); None where
+# the kernel has changed since its counters were taken
 TRAFFIC_BYTES_PER_NODE = {"fim_warp_kernel": (2.619382e9 + 3.100162e9) / 147783680,
                           "fim_cta_kernel<64>": (0.749040896e9 + 1.390257152e9) / 147783680,
-                          "fim_cta_kernel<128>": None, "fim_cta_kernel<256>": None, "fim_cta_kernel<512>": None}
+                          "fim_cta_kernel<128>": None, "fim_cta_kernel<256>": None,
+                          # the plain 256 x 256 x 32 medium, the only workload the bench runs with 512 threads
+                          "fim_cta_kernel<512>": (8.823296e6 + 0.104704e6) / 2097152}
 FP32_LANES = 128
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
 
@@ -273,7 +275,7 @@ def sweep_roofline(api, wl, theta, opts, steps, local, clock, nsm, ops_node, pre
     achieved = ops_node * nodes * steps / (ev_ms * 1e-3) / 1e12
     kname = _kernel_name(opts)
     per_launch_nodes = nodes * steps / max(launches, 1)
-    tb = TRAFFIC_BYTES_PER_NODE.get(kname)
+    tb = TRAFFIC_BYTES_PER_NODE.get(kname) if precision == "fp32" else None  # the captures are FP32 solves
     out = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "traffic": tb * per_launch_nodes if tb else None,
            "peak_source": peak_src,
